@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark of the triangle-counting hot path on GB300.
+
+One step = the whole hot path over one synthetic graph already resident in
+HBM: orientation by the degree order (tc_orient), exact count with per-vertex
+counts and clustering coefficients (tc_count_local), two-pass listing
+(tc_list_count + tc_list_write) and edge sparsification at q = 0.1
+(tc_sparsify_count).  The metric is oriented edges per second (m per step),
+with the intersection kernel's achieved fraction of the measured HBM roofline.
+
+Default workload: preferential attachment PA(n = 2^24, 16 edges per new
+vertex), ~268M undirected edges (edge list 2.1 GB, larger than L2, so no L2
+flush is needed between steps).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload ba24|ba27|rmat24|er]
+    python bench.py --impl reference   # the CPU oracle on a bounded sample
+Multi-GPU (torchrun, one rank per GPU): each rank counts its own independent
+graph (different seed); no collective on the data path (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "oriented edges/sec & HBM roofline %"
+UNIT = "oriented edges/s"
+
+WORKLOADS = {
+    "ba24": dict(kind="ba", n=1 << 24, k=16, label="preferential attachment PA(n=2^24, k=16)"),
+    "ba27": dict(kind="ba", n=1 << 27, k=16, label="preferential attachment PA(n=2^27, k=16)"),
+    "rmat24": dict(kind="rmat", scale=24, ef=16, label="R-MAT scale 24, edge factor 16 (0.57/0.19/0.19/0.05)"),
+    "er": dict(kind="er", n=16384, draws=131072, label="Erdos-Renyi G(n=16384, M=131072 draws)"),
+}
+
+
+def make_graph(w: dict, seed: int):
+    import synth
+    if w["kind"] == "ba":
+        return w["n"], synth.ba(w["n"], w["k"], seed)
+    if w["kind"] == "rmat":
+        return 1 << w["scale"], synth.rmat(w["scale"], w["ef"], seed)
+    return w["n"], synth.er(w["n"], w["draws"], seed)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_sha(*names) -> str:
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(ROOT, "paper_1706_05151_gb300", "csrc", nm), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    for r in rec.get("records", []):
+        if r.get("kernel") == kernel and r.get("workload") == workload and \
+                r.get("source_sha") == source_sha(*r.get("sources", [])):
+            return float(r["dram_bytes_per_launch"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.samples = []
+        self.proc = None
+        self.window = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def mark(self, start: float, end: float):
+        self.window = (start, end)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        lo, hi = self.window if self.window else (0, 1e18)
+        rows = [s for t, s in self.samples if lo - 0.15 <= t <= hi + 0.15] or [s for _, s in self.samples[-3:]]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            parts = [p.strip() for p in r.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_pipeline(n, e, q, seed):
+    """The oracle's version of one step: adjacency, NodeIterator++ with T_v and
+    listing, clustering, and the sparsified count.  Returns (seconds, m, T)."""
+    import oracle
+    t0 = time.perf_counter()
+    adj = oracle.Adjacency(n, e)
+    r = adj.count(local=True, listing=True)
+    oracle.clustering(adj.deg, r["tv"])
+    oracle.sparsify_count(n, e, seed, q)
+    return time.perf_counter() - t0, len(e), r["T"]
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import synth
+    sample_n = 1 << args.ref_log_n
+    n, e = sample_n, synth.ba(sample_n, 16, args.seed)
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt, m, T = cpu_oracle_pipeline(n, e, args.q, args.seed)
+        if i >= args.warmup:
+            times.append(dt)
+    t = statistics.mean(times)
+    value = len(e) / t
+    sample = (f"CPU oracle (NodeIterator++, 1 thread) on PA(n=2^{args.ref_log_n}, k=16), m={len(e)}, "
+              f"full step: adjacency, T, T_v, listing, C_v, sparsified count q={args.q}")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["label"], "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tc", choices=["tc", "reference"])
+    ap.add_argument("--workload", default="ba24", choices=sorted(WORKLOADS))
+    ap.add_argument("--q", type=float, default=0.1)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-log-n", type=int, default=20, help="log2 n of the CPU-baseline sample")
+    ap.add_argument("--ref-log-n", type=int, default=18, help="log2 n of each reference-arm step")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    import torch.distributed as dist
+    import paper_1706_05151_gb300 as tc
+    from paper_1706_05151_gb300 import build as tcbuild
+
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if rank == 0 or world == 1:
+        tcbuild.build()
+    if world > 1:
+        dist.barrier()
+    ctx = tc.Context(local_rank)
+    w = WORKLOADS[args.workload]
+    n, e_np = make_graph(w, args.seed + rank)
+    m = len(e_np)
+    edges_host = torch.from_numpy(e_np).pin_memory()
+    edges_dev = edges_host.to(dev)
+    q, seed = args.q, args.seed
+
+    def step():
+        g = tc.orient(edges_dev, n, ctx)
+        T, tv, cc = tc.count_local(g, True, ctx)
+        tri = tc.list_triangles(g, ctx)
+        sp = tc.sparsify_count(g, q, seed, ctx)
+        return g, T, tv, cc, tri, sp
+
+    for _ in range(args.warmup):
+        g, T, tv, cc, tri, sp = step()
+    W = int((g.deg.to(torch.int64) * g.dhat.to(torch.int64)).sum().item())
+    assert int(tv.sum().item()) == 3 * T and len(tri) == T
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        if not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        gpu_id = str(local_rank)
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.3)
+
+    # ---- timed region: K device-resident steps ----
+    ctx.reset_stats()
+    ctx.set_profiling(True)
+    stream = torch.cuda.current_stream(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.time()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    t_wall1 = time.time()
+    ctx.set_profiling(False)
+    launches = ctx.launches
+    stages = ctx.stages()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sampler.mark(t_wall0, t_wall1)
+    clocks = sampler.stop()
+
+    # ---- e2e: host buffers through the public API, copies inside the timed region ----
+    tv_host = torch.empty(n, dtype=torch.int64).pin_memory()
+    cc_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    tri_host = torch.empty((max(T, 1), 3), dtype=torch.int32).pin_memory()
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        ed = edges_host.to(dev, non_blocking=True)
+        g2 = tc.orient(ed, n, ctx)
+        T2, tv2, cc2 = tc.count_local(g2, True, ctx)
+        tri2 = tc.list_triangles(g2, ctx)
+        sp2 = tc.sparsify_count(g2, q, seed, ctx)
+        tv_host.copy_(tv2, non_blocking=True)
+        cc_host.copy_(cc2, non_blocking=True)
+        tri_host[: len(tri2)].copy_(tri2, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+        mt = torch.tensor([m], device=dev, dtype=torch.int64)
+        dist.all_reduce(mt)
+        m_total = int(mt.item())
+    else:
+        m_total = m
+
+    # ---- roofline of the intersection kernel (per-vertex counting pass) ----
+    peak, peak_src = load_peaks()
+    inter_ms = sum(stages.get(k, (0.0, 0))[0] for k in ("local.warp", "local.block"))
+    inter_calls = max(stages.get("local.warp", (0.0, 0))[1], 1)
+    inter_avg_ms = inter_ms / inter_calls
+    b_alg = 4 * W + 4 * m + 8 * (n + 1)
+    achieved = b_alg / (inter_avg_ms * 1e-3) / 1e9
+    traffic = recorded_traffic("local.warp", args.workload)
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            import synth
+            sn = 1 << args.cpu_log_n
+            se = synth.ba(sn, 16, args.seed)
+            dt, sm, _ = cpu_oracle_pipeline(sn, se, q, seed)
+            cpu = {"value": sm / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"CPU oracle (NodeIterator++, 1 thread) full step on PA(n=2^{args.cpu_log_n}, "
+                             f"k=16), m={sm}: adjacency, T, T_v, listing, C_v, sparsified count; {dt:.1f} s"}
+        h2d = 8 * m
+        d2h = 16 * n + 12 * T + 8 * 3
+        out = {
+            "metric": METRIC, "value": m_total / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": w["label"], "n": n, "m": m, "triangles": T, "W_sum_d_dhat": W,
+                       "q": q, "seed": args.seed,
+                       "step": "tc_orient + tc_count_local(C_v) + tc_list + tc_sparsify_count(q)",
+                       "l2": "inputs larger than L2 (edge list %.2f GB, CSR %.2f GB)" % (
+                           8 * m / 1e9, (4 * m + 8 * n) / 1e9),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_count_warp+k_count_block (tc_count_local)",
+                         "algorithmic_bytes": b_alg, "avg_launch_ms": inter_avg_ms, "peak_source": peak_src},
+            "e2e": {"value": m_total / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in sorted(stages.items())},
+            "cpu_baseline": cpu,
+            "sparsified": {"kept_edges": sp[1], "kept_triangles": sp[0], "estimate": sp[2],
+                           "rel_error": abs(sp[2] - T) / T if T else None},
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

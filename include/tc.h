@@ -1,0 +1,212 @@
+/*
+ * tc.h -- C ABI of libtc, exact triangle counting on one GPU (sm_103a).
+ *
+ * The library implements the hot path of Arifuzzaman, Khan and Marathe,
+ * "Distributed-Memory Parallel Algorithms for Counting and Listing Triangles
+ * in Big Graphs": orient an undirected simple graph by the degree order of
+ * Eq. (1) into sorted out-neighbour lists N_v (Definition 1, the preprocessing
+ * of NodeIteratorN, Figure 2), then sum |N_v intersect N_u| over every
+ * oriented edge (v, u) (Figure 2, counting loop; Theorem 1 shows each triangle
+ * is found once).  The same pass gives per-vertex counts T_v (Section 11,
+ * Figure "localcount"), local clustering coefficients C_v (Preliminaries),
+ * the triangle list (Section 10, Figure "tlisting") and the edge-sparsified
+ * estimate T'/q^3 (Section 9.1, Figure "sparsification").
+ *
+ * Conventions shared by every call:
+ *   - Vertex ids are int32 in [0, n); CSR offsets are int64; counts are
+ *     64-bit integers and exact.
+ *   - Pointers documented "device" must point to memory of the context's
+ *     device (cudaMalloc'd, e.g. by PyTorch); "host" pointers to host memory.
+ *   - The caller owns every buffer.  Calls that need scratch memory take a
+ *     device workspace `ws` of `ws_bytes` bytes, at least what
+ *     tc_workspace_size() reports for that operation and graph size, aligned
+ *     to 256 bytes.  No call allocates device memory after tc_ctx_create.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All
+ *     device work is enqueued on it.  In the default synchronous mode a call
+ *     returns after that work has finished and reports input errors found on
+ *     the device; after tc_ctx_set_async(ctx, 1) calls only enqueue and return
+ *     TC_OK, and tc_ctx_status() reports the device-side checks later.
+ *   - Errors are returned as tc_status, never by abort; tc_last_error(ctx)
+ *     gives a one-line description of the last failure on that context.
+ *   - A tc_ctx is not thread-safe: use one per host thread (or per stream).
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TC_OK = 0,
+  TC_ERR_INVALID_ARG = 1,   /* bad pointer, size or parameter (checked on the host) */
+  TC_ERR_INVALID_GRAPH = 2, /* id outside [0, n), self-loop, repeated edge or broken CSR */
+  TC_ERR_WORKSPACE = 3,     /* ws_bytes smaller than tc_workspace_size() */
+  TC_ERR_CAPACITY = 4,      /* listing output buffer too small */
+  TC_ERR_CUDA = 5,          /* a CUDA runtime call failed (see tc_last_error) */
+  TC_ERR_UNSUPPORTED = 6,   /* a size beyond a documented limit */
+  TC_ERR_TIMEOUT = 7,       /* a bounded wait ran out */
+  TC_ERR_REJECTED = 8,      /* admission refused (serving) */
+  TC_ERR_NOT_READY = 9      /* result not finished yet (serving) */
+} tc_status;
+
+/* Operations whose workspace size tc_workspace_size() reports. */
+typedef enum {
+  TC_OP_ORIENT = 0,
+  TC_OP_COUNT = 1,       /* tc_count and tc_count_local */
+  TC_OP_LIST = 2,        /* tc_list, tc_list_count, tc_list_write */
+  TC_OP_SPARSIFY = 3     /* tc_sparsify_count */
+} tc_op;
+
+typedef struct tc_ctx tc_ctx;
+typedef void* tc_stream; /* cudaStream_t */
+
+/*
+ * An oriented graph in device memory, as tc_orient produces it:
+ *   offsets[n+1]  int64, offsets[0] = 0, offsets[n] = m, non-decreasing;
+ *   cols[m]       int32, cols[offsets[v] .. offsets[v+1]) = N_v, the ids u with
+ *                 v preceding u in the order of Eq. (1), sorted ascending;
+ *   deg[n]        int32, the undirected degree d_v (may be NULL for tc_count,
+ *                 tc_list and tc_sparsify_count; required for clustering);
+ *   dhat[n]       int32, the effective degree |N_v| (Definition 1; optional).
+ * The counting calls need only a CSR whose lists are sorted, strictly
+ * increasing and form an acyclic orientation; they check offsets and ids
+ * against n and m and report TC_ERR_INVALID_GRAPH instead of reading out of
+ * bounds.
+ */
+typedef struct {
+  int32_t n;
+  int64_t m;
+  const int64_t* offsets;
+  const int32_t* cols;
+  const int32_t* deg;
+  const int32_t* dhat;
+} tc_graph;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context bound to CUDA device `device` (sets it current on this thread). */
+tc_status tc_ctx_create(int device, tc_ctx** out);
+void tc_ctx_destroy(tc_ctx* ctx);
+/* async = 1: calls only enqueue work; async = 0 (default): calls wait and check. */
+tc_status tc_ctx_set_async(tc_ctx* ctx, int async);
+/* Wait for `stream` and report the device-side checks of the calls enqueued since the last report. */
+tc_status tc_ctx_status(tc_ctx* ctx, tc_stream stream);
+const char* tc_status_string(tc_status s);
+const char* tc_last_error(const tc_ctx* ctx);
+/* Number of SMs of the context's device (sizes persistent grids). */
+int tc_ctx_sm_count(const tc_ctx* ctx);
+/* Library version string. */
+const char* tc_version(void);
+
+/*
+ * Per-stage timing and launch accounting (no counterpart in the paper; it
+ * measures this library).  With profiling on, each kernel group a call
+ * launches is bracketed by CUDA events on the call's stream; the totals are
+ * resolved (waiting on those events) when read.  Stage names are
+ * "<operation>.<kernel>", e.g. "local.warp" for the per-vertex counting kernel.
+ */
+tc_status tc_ctx_set_profiling(tc_ctx* ctx, int on);
+/* Number of stages seen so far (waits for pending stage events). */
+int tc_ctx_stage_count(tc_ctx* ctx);
+/* Stage i: *name (owned by ctx), total milliseconds and number of timed calls. */
+tc_status tc_ctx_stage(tc_ctx* ctx, int i, const char** name, double* ms, int64_t* calls);
+/* Clear stage totals and the launch counter. */
+tc_status tc_ctx_reset_stats(tc_ctx* ctx);
+/* Kernels this context has launched since creation or the last reset. */
+int64_t tc_ctx_launches(const tc_ctx* ctx);
+
+/*
+ * Bytes of device workspace operation `op` needs for a graph of n vertices
+ * and m edges (m undirected edges = m oriented edges).  Writes *bytes.
+ */
+tc_status tc_workspace_size(tc_op op, int32_t n, int64_t m, size_t* bytes);
+
+/* ---- orientation (Eq. (1), Definition 1, Figure 2 preprocessing) -------- */
+
+/*
+ * Build the oriented CSR of the undirected simple graph given as an edge list.
+ *   edges   device int32[m][2]: each undirected edge exactly once, either
+ *           direction, any order.
+ *   offsets device int64[n+1], cols device int32[m], deg device int32[n],
+ *   dhat    device int32[n]: outputs as described for tc_graph.
+ * The order is u precedes v iff d_u < d_v, or d_u = d_v and u < v (Eq. (1));
+ * each N_v is sorted ascending by id (Figure 2).  Ids outside [0, n),
+ * self-loops and repeated edges give TC_ERR_INVALID_GRAPH (outputs are then
+ * unspecified but every access stays in bounds).  Lists longer than 32768
+ * give TC_ERR_UNSUPPORTED (the order bounds |N_v| by sqrt(2m), so this needs
+ * m above about 5.4e8 and an adversarial graph).
+ */
+tc_status tc_orient(tc_ctx* ctx, int32_t n, int64_t m, const int32_t* edges, int64_t* offsets,
+                    int32_t* cols, int32_t* deg, int32_t* dhat, void* ws, size_t ws_bytes,
+                    tc_stream stream);
+
+/* ---- counting (Figure 2 counting loop; Theorems 1-2) --------------------- */
+
+/*
+ * T = sum over oriented edges (v, u) of |N_v intersect N_u|.
+ *   total_dev  device uint64[1], overwritten with T.
+ */
+tc_status tc_count(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, void* ws, size_t ws_bytes,
+                   tc_stream stream);
+
+/*
+ * T plus per-vertex counts (Section 11, Figure "localcount": each triangle
+ * adds one to each of its three vertices) and, if cc_dev is not NULL, the
+ * local clustering coefficients C_v = 2 T_v / (d_v (d_v - 1)) in float64,
+ * one IEEE division, C_v = 0 when d_v < 2 (needs g->deg).
+ *   total_dev device uint64[1]; tv_dev device int64[n]; cc_dev device double[n] or NULL.
+ */
+tc_status tc_count_local(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, int64_t* tv_dev,
+                         double* cc_dev, void* ws, size_t ws_bytes, tc_stream stream);
+
+/* ---- listing (Section 10, Figure "tlisting") ------------------------------ */
+
+/*
+ * Two-pass listing.  tc_list_count counts the triangles of each apex vertex v
+ * (the lowest of the three in the order), scans them into output positions
+ * kept in `ws`, and writes the total to total_dev (device int64[1]).
+ * tc_list_write, given the same g and ws right after tc_list_count, writes
+ * every triangle as an int32 triple (v, u, w) with v < u < w in the order,
+ * u in N_v and w in N_v intersect N_u, into tri_dev (device int32[cap][3]).
+ * Triples of one apex vertex are contiguous; apex vertices appear in id order.
+ * If the total exceeds cap nothing is written and the device-side check
+ * reports TC_ERR_CAPACITY.
+ */
+tc_status tc_list_count(tc_ctx* ctx, const tc_graph* g, int64_t* total_dev, void* ws, size_t ws_bytes,
+                        tc_stream stream);
+tc_status tc_list_write(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_t cap, void* ws,
+                        size_t ws_bytes, tc_stream stream);
+/*
+ * Both passes in one call.  Waits for the count (even in async mode) to check
+ * it against cap.  *count_out (host) receives the number of triangles; with
+ * TC_ERR_CAPACITY it holds the capacity needed and nothing was written.
+ */
+tc_status tc_list(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_t cap, int64_t* count_out,
+                  void* ws, size_t ws_bytes, tc_stream stream);
+
+/* ---- sparsification (Section 9.1, Figure "sparsification") ---------------- */
+
+/*
+ * Keep each undirected edge {a, b} independently with probability q and
+ * count the triangles T' of the kept graph, whose orientation is the one of
+ * the ORIGINAL degrees (the order is fixed before sampling).  The coin of
+ * {a, b} is Philox4x64-10 (Salmon et al., SC'11) with counter
+ * (min(a,b), max(a,b), 0, 0) and key (seed, 0): keep iff (w0 >> 11) < ceil(q * 2^53),
+ * i.e. (w0 >> 11) * 2^-53 < q, where w0 is the first output word.
+ *   q in [0, 1]; kept_tri_dev device uint64[1] (T'); kept_edges_dev device
+ *   int64[1] (edges kept).  The unbiased estimate of T is T' / q^3 (Section 9.1),
+ *   computed by the caller on the host.
+ */
+tc_status tc_sparsify_count(tc_ctx* ctx, const tc_graph* g, double q, uint64_t seed,
+                            uint64_t* kept_tri_dev, int64_t* kept_edges_dev, void* ws, size_t ws_bytes,
+                            tc_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

@@ -1,0 +1,288 @@
+"""Python binding of libtc (include/tc.h): exact triangle counting on one GPU.
+
+Thin ctypes marshalling over the C ABI.  PyTorch supplies device memory and
+the current CUDA stream; every step of the computation runs in the library's
+own CUDA kernels.  There is no CPU fallback: if ``libtc.so`` has not been
+built (``python -m paper_1706_05151_gb300.build``) or no GPU is present, the
+calls raise.
+
+The functions mirror the C entry points:
+    orient            tc_orient          Eq. (1), Definition 1, Figure 2 preprocessing
+    count             tc_count           Figure 2 counting loop (Theorems 1-2)
+    count_local       tc_count_local     Section 11 (T_v) and C_v (Preliminaries)
+    list_triangles    tc_list_count + tc_list_write   Section 10
+    sparsify_count    tc_sparsify_count  Section 9.1
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtc.so")
+
+TC_OP_ORIENT, TC_OP_COUNT, TC_OP_LIST, TC_OP_SPARSIFY = 0, 1, 2, 3
+STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_INVALID_GRAPH", 3: "TC_ERR_WORKSPACE",
+          4: "TC_ERR_CAPACITY", 5: "TC_ERR_CUDA", 6: "TC_ERR_UNSUPPORTED", 7: "TC_ERR_TIMEOUT",
+          8: "TC_ERR_REJECTED", 9: "TC_ERR_NOT_READY"}
+
+# every symbol include/tc.h declares
+EXPORTS = ["tc_ctx_create", "tc_ctx_destroy", "tc_ctx_set_async", "tc_ctx_status", "tc_status_string",
+           "tc_last_error", "tc_ctx_sm_count", "tc_version", "tc_workspace_size", "tc_orient", "tc_count",
+           "tc_count_local", "tc_list_count", "tc_list_write", "tc_list", "tc_sparsify_count",
+           "tc_ctx_set_profiling", "tc_ctx_stage_count", "tc_ctx_stage", "tc_ctx_reset_stats", "tc_ctx_launches"]
+
+
+class TcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class TcGraph(ctypes.Structure):
+    """Mirror of the C struct tc_graph."""
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int64), ("offsets", ctypes.c_void_p),
+                ("cols", ctypes.c_void_p), ("deg", ctypes.c_void_p), ("dhat", ctypes.c_void_p)]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+vp, i32, i64, u64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtc.so (raises if it is missing: the library has no fallback path)."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is not built; run `python -m paper_1706_05151_gb300.build` "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        G = ctypes.POINTER(TcGraph)
+        sigs = {
+            "tc_ctx_create": (i32, [ctypes.c_int, ctypes.POINTER(vp)]),
+            "tc_ctx_destroy": (None, [vp]),
+            "tc_ctx_set_async": (i32, [vp, ctypes.c_int]),
+            "tc_ctx_status": (i32, [vp, vp]),
+            "tc_status_string": (ctypes.c_char_p, [i32]),
+            "tc_last_error": (ctypes.c_char_p, [vp]),
+            "tc_ctx_sm_count": (ctypes.c_int, [vp]),
+            "tc_version": (ctypes.c_char_p, []),
+            "tc_workspace_size": (i32, [ctypes.c_int, i32, i64, ctypes.POINTER(sz)]),
+            "tc_orient": (i32, [vp, i32, i64, vp, vp, vp, vp, vp, vp, sz, vp]),
+            "tc_count": (i32, [vp, G, vp, vp, sz, vp]),
+            "tc_count_local": (i32, [vp, G, vp, vp, vp, vp, sz, vp]),
+            "tc_list_count": (i32, [vp, G, vp, vp, sz, vp]),
+            "tc_list_write": (i32, [vp, G, vp, i64, vp, sz, vp]),
+            "tc_list": (i32, [vp, G, vp, i64, ctypes.POINTER(i64), vp, sz, vp]),
+            "tc_sparsify_count": (i32, [vp, G, ctypes.c_double, u64, vp, vp, vp, sz, vp]),
+            "tc_ctx_set_profiling": (i32, [vp, ctypes.c_int]),
+            "tc_ctx_stage_count": (ctypes.c_int, [vp]),
+            "tc_ctx_stage": (i32, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
+            "tc_ctx_reset_stats": (i32, [vp]),
+            "tc_ctx_launches": (i64, [vp]),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device: torch.device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Context:
+    """A tc_ctx bound to one CUDA device, with a reusable device workspace."""
+
+    def __init__(self, device: int | torch.device = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libtc needs a CUDA GPU; none is available (there is no CPU fallback)")
+        self.lib = load_library()
+        self.device = torch.device("cuda", device if isinstance(device, int) else device.index or 0)
+        h = vp()
+        st = self.lib.tc_ctx_create(self.device.index, ctypes.byref(h))
+        if st != 0:
+            raise TcError(st, "tc_ctx_create failed")
+        self.handle = h
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.tc_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, st: int):
+        if st != 0:
+            raise TcError(st, self.lib.tc_last_error(self.handle).decode())
+
+    @property
+    def sm_count(self) -> int:
+        return int(self.lib.tc_ctx_sm_count(self.handle))
+
+    def set_async(self, on: bool):
+        self.check(self.lib.tc_ctx_set_async(self.handle, 1 if on else 0))
+
+    def status(self):
+        self.check(self.lib.tc_ctx_status(self.handle, _stream(self.device)))
+
+    def set_profiling(self, on: bool):
+        self.check(self.lib.tc_ctx_set_profiling(self.handle, 1 if on else 0))
+
+    def reset_stats(self):
+        self.check(self.lib.tc_ctx_reset_stats(self.handle))
+
+    @property
+    def launches(self) -> int:
+        """Kernels this context launched since creation or the last reset_stats()."""
+        return int(self.lib.tc_ctx_launches(self.handle))
+
+    def stages(self) -> dict:
+        """{stage name: (total ms, timed calls)} of the profiled kernel groups."""
+        out = {}
+        for i in range(int(self.lib.tc_ctx_stage_count(self.handle))):
+            name, ms, calls = ctypes.c_char_p(), ctypes.c_double(), i64()
+            self.check(self.lib.tc_ctx_stage(self.handle, i, ctypes.byref(name), ctypes.byref(ms),
+                                             ctypes.byref(calls)))
+            out[name.value.decode()] = (float(ms.value), int(calls.value))
+        return out
+
+    def workspace_size(self, op: int, n: int, m: int) -> int:
+        b = sz(0)
+        self.check(self.lib.tc_workspace_size(op, n, m, ctypes.byref(b)))
+        return int(b.value)
+
+    def workspace(self, op: int, n: int, m: int) -> torch.Tensor:
+        need = self.workspace_size(op, n, m)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+        return self._ws
+
+
+_default_ctx: dict[int, Context] = {}
+
+
+def default_context(device: int = 0) -> Context:
+    if device not in _default_ctx:
+        _default_ctx[device] = Context(device)
+    return _default_ctx[device]
+
+
+@dataclass
+class Graph:
+    """An oriented graph in device memory (the C struct tc_graph)."""
+    n: int
+    m: int
+    offsets: torch.Tensor  # int64[n+1]
+    cols: torch.Tensor     # int32[m]
+    deg: torch.Tensor | None = None   # int32[n]
+    dhat: torch.Tensor | None = None  # int32[n]
+
+    def struct(self) -> TcGraph:
+        return TcGraph(self.n, self.m, self.offsets.data_ptr(), self.cols.data_ptr() if self.m else None,
+                       self.deg.data_ptr() if self.deg is not None else None,
+                       self.dhat.data_ptr() if self.dhat is not None else None)
+
+
+def orient(edges: torch.Tensor, n: int, ctx: Context | None = None) -> Graph:
+    """tc_orient: edges int32[m, 2] on the GPU (each undirected edge once) -> oriented CSR."""
+    ctx = ctx or default_context()
+    dev = ctx.device
+    if edges.device != dev or edges.dtype != torch.int32 or edges.dim() != 2 or edges.shape[1] != 2:
+        raise ValueError("edges must be an int32 [m, 2] tensor on the context's device")
+    edges = edges.contiguous()
+    m = int(edges.shape[0])
+    offsets = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    cols = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+    deg = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    dhat = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    ws = ctx.workspace(TC_OP_ORIENT, n, m)
+    ctx.check(ctx.lib.tc_orient(ctx.handle, n, m, _ptr(edges) if m else None, _ptr(offsets), _ptr(cols),
+                                _ptr(deg), _ptr(dhat), _ptr(ws), ws.numel(), _stream(dev)))
+    return Graph(n, m, offsets, cols[:m], deg[:n], dhat[:n])
+
+
+def count(g: Graph, ctx: Context | None = None, out: torch.Tensor | None = None) -> int:
+    """tc_count: the exact triangle count T."""
+    ctx = ctx or default_context()
+    total = out if out is not None else torch.empty(1, dtype=torch.int64, device=ctx.device)
+    ws = ctx.workspace(TC_OP_COUNT, g.n, g.m)
+    ctx.check(ctx.lib.tc_count(ctx.handle, ctypes.byref(g.struct()), _ptr(total), _ptr(ws), ws.numel(),
+                               _stream(ctx.device)))
+    return int(total.item()) if out is None else total
+
+
+def count_local(g: Graph, clustering: bool = True, ctx: Context | None = None):
+    """tc_count_local: (T, T_v int64[n], C_v float64[n] or None)."""
+    ctx = ctx or default_context()
+    total = torch.empty(1, dtype=torch.int64, device=ctx.device)
+    tv = torch.empty(max(g.n, 1), dtype=torch.int64, device=ctx.device)
+    cc = torch.empty(max(g.n, 1), dtype=torch.float64, device=ctx.device) if clustering else None
+    ws = ctx.workspace(TC_OP_COUNT, g.n, g.m)
+    ctx.check(ctx.lib.tc_count_local(ctx.handle, ctypes.byref(g.struct()), _ptr(total), _ptr(tv), _ptr(cc),
+                                     _ptr(ws), ws.numel(), _stream(ctx.device)))
+    return int(total.item()), tv[: g.n], (cc[: g.n] if cc is not None else None)
+
+
+def list_triangles(g: Graph, ctx: Context | None = None) -> torch.Tensor:
+    """tc_list_count then tc_list_write: int32[T, 3] triples (v, u, w), v < u < w in the order."""
+    ctx = ctx or default_context()
+    total = torch.empty(1, dtype=torch.int64, device=ctx.device)
+    ws = ctx.workspace(TC_OP_LIST, g.n, g.m)
+    gs = g.struct()
+    ctx.check(ctx.lib.tc_list_count(ctx.handle, ctypes.byref(gs), _ptr(total), _ptr(ws), ws.numel(),
+                                    _stream(ctx.device)))
+    T = int(total.item())
+    tri = torch.empty((max(T, 1), 3), dtype=torch.int32, device=ctx.device)
+    ctx.check(ctx.lib.tc_list_write(ctx.handle, ctypes.byref(gs), _ptr(tri), T, _ptr(ws), ws.numel(),
+                                    _stream(ctx.device)))
+    return tri[:T]
+
+
+def list_triangles_into(g: Graph, tri: torch.Tensor, ctx: Context | None = None) -> int:
+    """tc_list: both passes into a caller buffer int32[cap, 3]; returns T (raises TC_ERR_CAPACITY)."""
+    ctx = ctx or default_context()
+    ws = ctx.workspace(TC_OP_LIST, g.n, g.m)
+    cnt = i64(0)
+    ctx.check(ctx.lib.tc_list(ctx.handle, ctypes.byref(g.struct()), _ptr(tri), int(tri.shape[0]),
+                              ctypes.byref(cnt), _ptr(ws), ws.numel(), _stream(ctx.device)))
+    return int(cnt.value)
+
+
+def sparsify_count(g: Graph, q: float, seed: int, ctx: Context | None = None):
+    """tc_sparsify_count: (T' of the kept graph, kept edges, estimate T'/q^3)."""
+    ctx = ctx or default_context()
+    kept_tri = torch.empty(1, dtype=torch.int64, device=ctx.device)
+    kept_edges = torch.empty(1, dtype=torch.int64, device=ctx.device)
+    ws = ctx.workspace(TC_OP_SPARSIFY, g.n, g.m)
+    ctx.check(ctx.lib.tc_sparsify_count(ctx.handle, ctypes.byref(g.struct()), float(q), int(seed),
+                                        _ptr(kept_tri), _ptr(kept_edges), _ptr(ws), ws.numel(),
+                                        _stream(ctx.device)))
+    t = int(kept_tri.item())
+    est = float(t) / (q * q * q) if q > 0 else float("nan")
+    return t, int(kept_edges.item()), est
+
+
+def graph_from_csr(offsets: torch.Tensor, cols: torch.Tensor, deg=None, dhat=None) -> Graph:
+    """Wrap an existing oriented CSR (device tensors) as a Graph."""
+    n = int(offsets.numel()) - 1
+    return Graph(n, int(cols.numel()), offsets, cols, deg, dhat)

@@ -1,0 +1,397 @@
+// The extern "C" entry points of libtc (declared in include/tc.h): argument
+// checks on the host, workspace carving, device error-word handling, and the
+// stream-ordered launch sequences of the other translation units.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "tc_internal.cuh"
+
+using tc::Carver;
+using tc::Ctx;
+
+struct tc_ctx : public Ctx {};
+
+namespace {
+
+tc_status fail(tc_ctx* ctx, tc_status st, const char* fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->last_error, sizeof(ctx->last_error), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+tc_status cuda_fail(tc_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, TC_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+tc_status status_from_bits(tc_ctx* ctx, uint32_t bits) {
+  if (bits == 0) return TC_OK;
+  if (bits & tc::ERR_BAD_ID) return fail(ctx, TC_ERR_INVALID_GRAPH, "vertex id outside [0, n)");
+  if (bits & tc::ERR_SELF_LOOP) return fail(ctx, TC_ERR_INVALID_GRAPH, "self-loop in the edge list");
+  if (bits & tc::ERR_DUPLICATE) return fail(ctx, TC_ERR_INVALID_GRAPH, "repeated edge in the edge list");
+  if (bits & tc::ERR_BAD_CSR) return fail(ctx, TC_ERR_INVALID_GRAPH, "offsets not monotone or outside [0, m]");
+  if (bits & tc::ERR_TOO_LONG) return fail(ctx, TC_ERR_UNSUPPORTED, "an oriented list exceeds the supported length");
+  if (bits & tc::ERR_CAPACITY) return fail(ctx, TC_ERR_CAPACITY, "listing output buffer too small");
+  if (bits & tc::ERR_TIMEOUT) return fail(ctx, TC_ERR_TIMEOUT, "a bounded device wait ran out");
+  return fail(ctx, TC_ERR_CUDA, "unknown device error bits 0x%x", bits);
+}
+
+// Start of a call: in synchronous mode the error word is cleared for this call.
+tc_status begin(tc_ctx* ctx, cudaStream_t s) {
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, TC_ERR_CUDA, "cudaSetDevice failed");
+  if (!ctx->async) {
+    cudaError_t e = cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "clear error word");
+  }
+  return TC_OK;
+}
+
+// End of a call: in synchronous mode wait for the stream and read the error word.
+tc_status finish(tc_ctx* ctx, cudaStream_t s, cudaError_t launch) {
+  if (launch != cudaSuccess) return cuda_fail(ctx, launch, "launch");
+  if (ctx->async) return TC_OK;
+  cudaError_t e = cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+  return status_from_bits(ctx, *ctx->h_err);
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+tc_status check_ws(tc_ctx* ctx, tc_op op, int32_t n, int64_t m, void* ws, size_t ws_bytes) {
+  size_t need = 0;
+  tc_status st = tc_workspace_size(op, n, m, &need);
+  if (st != TC_OK) return fail(ctx, st, "bad sizes n=%d m=%lld", n, static_cast<long long>(m));
+  if (ws_bytes < need)
+    return fail(ctx, TC_ERR_WORKSPACE, "workspace %zu bytes, need %zu", ws_bytes, need);
+  if (need > 0 && (!ws || !aligned(ws, 256))) return fail(ctx, TC_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+  return TC_OK;
+}
+
+tc_status check_graph(tc_ctx* ctx, const tc_graph* g) {
+  if (!ctx) return TC_ERR_INVALID_ARG;
+  if (!g) return fail(ctx, TC_ERR_INVALID_ARG, "graph is NULL");
+  if (g->n < 0 || g->m < 0) return fail(ctx, TC_ERR_INVALID_ARG, "negative n or m");
+  if (!g->offsets) return fail(ctx, TC_ERR_INVALID_ARG, "offsets is NULL");
+  if (g->m > 0 && !g->cols) return fail(ctx, TC_ERR_INVALID_ARG, "cols is NULL");
+  if (!aligned(g->offsets, 8)) return fail(ctx, TC_ERR_INVALID_ARG, "offsets not 8-byte aligned");
+  return TC_OK;
+}
+
+cudaEvent_t take_event(Ctx* ctx) {
+  auto& pool = ctx->prof.pool;
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void resolve_stages(Ctx* ctx) {
+  for (auto& p : ctx->prof.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.stop) == cudaSuccess && cudaEventElapsedTime(&ms, p.start, p.stop) == cudaSuccess) {
+      ctx->prof.totals[p.index].ms += ms;
+      ctx->prof.totals[p.index].calls += 1;
+    }
+    ctx->prof.pool.push_back(p.start);
+    ctx->prof.pool.push_back(p.stop);
+  }
+  ctx->prof.pending.clear();
+}
+
+}  // namespace
+
+namespace tc {
+
+Stage::Stage(Ctx* ctx, cudaStream_t s, const char* name) : ctx_(ctx), s_(s) {
+  if (!ctx->prof.on) return;
+  auto& t = ctx->prof.totals;
+  for (size_t i = 0; i < t.size(); ++i)
+    if (t[i].name == name) index_ = static_cast<int>(i);
+  if (index_ < 0) {
+    t.push_back(StageTotal{name, 0.0, 0});
+    index_ = static_cast<int>(t.size()) - 1;
+  }
+  start_ = take_event(ctx);
+  cudaEventRecord(start_, s);
+}
+
+Stage::~Stage() {
+  if (index_ < 0) return;
+  cudaEvent_t stop = take_event(ctx_);
+  cudaEventRecord(stop, s_);
+  ctx_->prof.pending.push_back(PendingStage{index_, start_, stop});
+}
+
+}  // namespace tc
+
+extern "C" {
+
+const char* tc_version(void) { return "libtc 0.1 (sm_103a)"; }
+
+const char* tc_status_string(tc_status s) {
+  switch (s) {
+    case TC_OK: return "ok";
+    case TC_ERR_INVALID_ARG: return "invalid argument";
+    case TC_ERR_INVALID_GRAPH: return "invalid graph";
+    case TC_ERR_WORKSPACE: return "workspace too small";
+    case TC_ERR_CAPACITY: return "output capacity too small";
+    case TC_ERR_CUDA: return "CUDA error";
+    case TC_ERR_UNSUPPORTED: return "unsupported size";
+    case TC_ERR_TIMEOUT: return "timeout";
+    case TC_ERR_REJECTED: return "rejected";
+    case TC_ERR_NOT_READY: return "not ready";
+  }
+  return "unknown status";
+}
+
+tc_status tc_ctx_create(int device, tc_ctx** out) {
+  if (!out) return TC_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return TC_ERR_INVALID_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return TC_ERR_CUDA;
+  tc_ctx* c = new tc_ctx();
+  c->device = device;
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+  c->sm_count = v > 0 ? v : 1;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  c->smem_optin = static_cast<size_t>(v);
+  if (cudaMalloc(&c->d_err, sizeof(uint32_t)) != cudaSuccess ||
+      cudaHostAlloc(reinterpret_cast<void**>(&c->h_err), sizeof(uint32_t), cudaHostAllocDefault) != cudaSuccess ||
+      cudaMemset(c->d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
+    if (c->d_err) cudaFree(c->d_err);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    delete c;
+    return TC_ERR_CUDA;
+  }
+  *c->h_err = 0;
+  *out = c;
+  return TC_OK;
+}
+
+void tc_ctx_destroy(tc_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  resolve_stages(ctx);
+  for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+  cudaFree(ctx->d_err);
+  cudaFreeHost(ctx->h_err);
+  delete ctx;
+}
+
+tc_status tc_ctx_set_async(tc_ctx* ctx, int async) {
+  if (!ctx) return TC_ERR_INVALID_ARG;
+  ctx->async = async ? 1 : 0;
+  return TC_OK;
+}
+
+tc_status tc_ctx_status(tc_ctx* ctx, tc_stream stream) {
+  if (!ctx) return TC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "status");
+  return status_from_bits(ctx, *ctx->h_err);
+}
+
+tc_status tc_ctx_set_profiling(tc_ctx* ctx, int on) {
+  if (!ctx) return TC_ERR_INVALID_ARG;
+  ctx->prof.on = on != 0;
+  return TC_OK;
+}
+
+int tc_ctx_stage_count(tc_ctx* ctx) {
+  if (!ctx) return 0;
+  resolve_stages(ctx);
+  return static_cast<int>(ctx->prof.totals.size());
+}
+
+tc_status tc_ctx_stage(tc_ctx* ctx, int i, const char** name, double* ms, int64_t* calls) {
+  if (!ctx) return TC_ERR_INVALID_ARG;
+  resolve_stages(ctx);
+  if (i < 0 || i >= static_cast<int>(ctx->prof.totals.size())) return TC_ERR_INVALID_ARG;
+  const tc::StageTotal& t = ctx->prof.totals[static_cast<size_t>(i)];
+  if (name) *name = t.name.c_str();
+  if (ms) *ms = t.ms;
+  if (calls) *calls = t.calls;
+  return TC_OK;
+}
+
+tc_status tc_ctx_reset_stats(tc_ctx* ctx) {
+  if (!ctx) return TC_ERR_INVALID_ARG;
+  resolve_stages(ctx);
+  ctx->prof.totals.clear();
+  ctx->launches = 0;
+  return TC_OK;
+}
+
+int64_t tc_ctx_launches(const tc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+const char* tc_last_error(const tc_ctx* ctx) { return ctx ? ctx->last_error : "no context"; }
+
+int tc_ctx_sm_count(const tc_ctx* ctx) { return ctx ? ctx->sm_count : 0; }
+
+tc_status tc_workspace_size(tc_op op, int32_t n, int64_t m, size_t* bytes) {
+  if (!bytes || n < 0 || m < 0) return TC_ERR_INVALID_ARG;
+  Carver c(nullptr);
+  switch (op) {
+    case TC_OP_ORIENT: tc::carve_orient(c, n, m); break;
+    case TC_OP_COUNT: tc::carve_count(c, n, false); break;
+    case TC_OP_LIST: tc::carve_count(c, n, true); break;
+    case TC_OP_SPARSIFY: tc::carve_sparsify(c, n, m); break;
+    default: return TC_ERR_INVALID_ARG;
+  }
+  *bytes = c.size();
+  return TC_OK;
+}
+
+tc_status tc_orient(tc_ctx* ctx, int32_t n, int64_t m, const int32_t* edges, int64_t* offsets, int32_t* cols,
+                    int32_t* deg, int32_t* dhat, void* ws, size_t ws_bytes, tc_stream stream) {
+  if (!ctx) return TC_ERR_INVALID_ARG;
+  if (n < 0 || m < 0) return fail(ctx, TC_ERR_INVALID_ARG, "negative n or m");
+  if (!offsets || (n > 0 && (!deg || !dhat)) || (m > 0 && (!edges || !cols)))
+    return fail(ctx, TC_ERR_INVALID_ARG, "NULL buffer");
+  if (m > 0 && !aligned(edges, 8)) return fail(ctx, TC_ERR_INVALID_ARG, "edges not 8-byte aligned");
+  if (!aligned(offsets, 8)) return fail(ctx, TC_ERR_INVALID_ARG, "offsets not 8-byte aligned");
+  tc_status st = check_ws(ctx, TC_OP_ORIENT, n, m, ws, ws_bytes);
+  if (st != TC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = begin(ctx, s)) != TC_OK) return st;
+  Carver c(ws);
+  tc::OrientWs w = tc::carve_orient(c, n, m);
+  return finish(ctx, s, tc::launch_orient(ctx, n, m, edges, offsets, cols, deg, dhat, w, s));
+}
+
+static tc_status count_impl(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, int64_t* tv_dev, double* cc_dev,
+                            void* ws, size_t ws_bytes, cudaStream_t s) {
+  tc_status st = check_graph(ctx, g);
+  if (st != TC_OK) return st;
+  if (!total_dev) return fail(ctx, TC_ERR_INVALID_ARG, "total_dev is NULL");
+  const bool local = tv_dev != nullptr;
+  if (cc_dev && (!local || !g->deg)) return fail(ctx, TC_ERR_INVALID_ARG, "clustering needs tv_dev and g->deg");
+  if ((st = check_ws(ctx, TC_OP_COUNT, g->n, g->m, ws, ws_bytes)) != TC_OK) return st;
+  if ((st = begin(ctx, s)) != TC_OK) return st;
+  Carver c(ws);
+  tc::CountWs w = tc::carve_count(c, g->n, false);
+  cudaError_t e = cudaMemsetAsync(total_dev, 0, sizeof(uint64_t), s);
+  if (e == cudaSuccess && local) e = cudaMemsetAsync(tv_dev, 0, sizeof(int64_t) * static_cast<size_t>(g->n), s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "clear outputs");
+  tc::CountArgs a{g->n, g->m, g->offsets, g->cols, reinterpret_cast<unsigned long long*>(total_dev), tv_dev,
+                  nullptr, 0};
+  e = tc::launch_count(ctx, local ? tc::MODE_LOCAL : tc::MODE_COUNT, a, w, s);
+  if (e == cudaSuccess && cc_dev) e = tc::launch_clustering(ctx, g->n, g->deg, tv_dev, cc_dev, s);
+  return finish(ctx, s, e);
+}
+
+tc_status tc_count(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, void* ws, size_t ws_bytes, tc_stream stream) {
+  return count_impl(ctx, g, total_dev, nullptr, nullptr, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+tc_status tc_count_local(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, int64_t* tv_dev, double* cc_dev,
+                         void* ws, size_t ws_bytes, tc_stream stream) {
+  if (ctx && !tv_dev) return fail(ctx, TC_ERR_INVALID_ARG, "tv_dev is NULL");
+  return count_impl(ctx, g, total_dev, tv_dev, cc_dev, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+tc_status tc_list_count(tc_ctx* ctx, const tc_graph* g, int64_t* total_dev, void* ws, size_t ws_bytes,
+                        tc_stream stream) {
+  tc_status st = check_graph(ctx, g);
+  if (st != TC_OK) return st;
+  if (!total_dev) return fail(ctx, TC_ERR_INVALID_ARG, "total_dev is NULL");
+  if ((st = check_ws(ctx, TC_OP_LIST, g->n, g->m, ws, ws_bytes)) != TC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = begin(ctx, s)) != TC_OK) return st;
+  Carver c(ws);
+  tc::CountWs w = tc::carve_count(c, g->n, true);
+  cudaError_t e = cudaMemsetAsync(total_dev, 0, sizeof(int64_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.vcount, 0, sizeof(int64_t) * (static_cast<size_t>(g->n) + 1), s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "clear outputs");
+  tc::CountArgs a{g->n, g->m, g->offsets, g->cols, reinterpret_cast<unsigned long long*>(total_dev), nullptr,
+                  nullptr, 0};
+  e = tc::launch_count(ctx, tc::MODE_LIST_COUNT, a, w, s);
+  if (e == cudaSuccess) {
+    tc::Stage st(ctx, s, "list_count.scan");
+    e = tc::exclusive_scan_i64(w.vcount, w.voff, g->n, w.scan, s);
+    tc::counted(ctx, g->n > 0 ? 3 : 1);
+  }
+  return finish(ctx, s, e);
+}
+
+tc_status tc_list_write(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_t cap, void* ws, size_t ws_bytes,
+                        tc_stream stream) {
+  tc_status st = check_graph(ctx, g);
+  if (st != TC_OK) return st;
+  if (cap < 0 || (cap > 0 && !tri_dev)) return fail(ctx, TC_ERR_INVALID_ARG, "bad output buffer");
+  if ((st = check_ws(ctx, TC_OP_LIST, g->n, g->m, ws, ws_bytes)) != TC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = begin(ctx, s)) != TC_OK) return st;
+  Carver c(ws);
+  tc::CountWs w = tc::carve_count(c, g->n, true);
+  tc::CountArgs a{g->n, g->m, g->offsets, g->cols, nullptr, nullptr, tri_dev, cap};
+  return finish(ctx, s, tc::launch_count(ctx, tc::MODE_LIST_WRITE, a, w, s));
+}
+
+tc_status tc_list(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_t cap, int64_t* count_out, void* ws,
+                  size_t ws_bytes, tc_stream stream) {
+  if (!ctx) return TC_ERR_INVALID_ARG;
+  if (!count_out) return fail(ctx, TC_ERR_INVALID_ARG, "count_out is NULL");
+  tc_status st = check_graph(ctx, g);
+  if (st != TC_OK) return st;
+  if ((st = check_ws(ctx, TC_OP_LIST, g->n, g->m, ws, ws_bytes)) != TC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Carver c(ws);
+  tc::CountWs w = tc::carve_count(c, g->n, true);
+  // the total lands in the last entry of the offsets the count pass scans
+  int64_t* total_dev = w.voff + g->n;
+  const int was_async = ctx->async;
+  ctx->async = 0;
+  st = tc_list_count(ctx, g, w.vcount + g->n, ws, ws_bytes, stream);
+  ctx->async = was_async;
+  if (st != TC_OK) return st;
+  int64_t total = 0;
+  cudaError_t e = cudaMemcpyAsync(&total, total_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "read listing total");
+  *count_out = total;
+  if (total > cap) return fail(ctx, TC_ERR_CAPACITY, "listing needs %lld triples, capacity %lld",
+                               static_cast<long long>(total), static_cast<long long>(cap));
+  return tc_list_write(ctx, g, tri_dev, cap, ws, ws_bytes, stream);
+}
+
+tc_status tc_sparsify_count(tc_ctx* ctx, const tc_graph* g, double q, uint64_t seed, uint64_t* kept_tri_dev,
+                            int64_t* kept_edges_dev, void* ws, size_t ws_bytes, tc_stream stream) {
+  tc_status st = check_graph(ctx, g);
+  if (st != TC_OK) return st;
+  if (!(q >= 0.0 && q <= 1.0)) return fail(ctx, TC_ERR_INVALID_ARG, "q must be in [0, 1]");
+  if (!kept_tri_dev || !kept_edges_dev) return fail(ctx, TC_ERR_INVALID_ARG, "NULL output");
+  if ((st = check_ws(ctx, TC_OP_SPARSIFY, g->n, g->m, ws, ws_bytes)) != TC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = begin(ctx, s)) != TC_OK) return st;
+  Carver c(ws);
+  tc::SparsifyWs w = tc::carve_sparsify(c, g->n, g->m);
+  // keep iff (w0 >> 11) * 2^-53 < q  <=>  (w0 >> 11) < ceil(q * 2^53); q * 2^53 is exact
+  const uint64_t t53 = static_cast<uint64_t>(std::ceil(q * 9007199254740992.0));
+  cudaError_t e = cudaMemsetAsync(kept_tri_dev, 0, sizeof(uint64_t), s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "clear outputs");
+  e = tc::launch_sparsify(ctx, g->n, g->m, g->offsets, g->cols, t53, seed, w, kept_edges_dev, s);
+  if (e == cudaSuccess) {
+    tc::CountArgs a{g->n, g->m, w.offsets, w.cols, reinterpret_cast<unsigned long long*>(kept_tri_dev), nullptr,
+                    nullptr, 0};
+    e = tc::launch_count(ctx, tc::MODE_COUNT, a, w.count, s);
+  }
+  return finish(ctx, s, e);
+}
+
+}  // extern "C"

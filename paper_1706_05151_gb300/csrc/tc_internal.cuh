@@ -1,0 +1,167 @@
+// Internal declarations shared by the libtc translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "tc.h"
+
+namespace tc {
+
+// Bits of the device error word.  Kernels OR them in instead of faulting.
+enum : uint32_t {
+  ERR_BAD_ID = 1u << 0,     // vertex id outside [0, n)
+  ERR_SELF_LOOP = 1u << 1,  // edge (v, v)
+  ERR_DUPLICATE = 1u << 2,  // the same edge twice
+  ERR_BAD_CSR = 1u << 3,    // offsets not monotone / outside [0, m]
+  ERR_TOO_LONG = 1u << 4,   // a list longer than a documented limit
+  ERR_CAPACITY = 1u << 5,   // listing output too small
+  ERR_TIMEOUT = 1u << 6,    // a bounded wait ran out
+};
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kSortBlockCap = 32768;     // longest list tc_orient sorts (ints in shared memory)
+constexpr int kMaxListLen = 1 << 24;     // longest list the counting kernels accept
+
+// Optional per-stage timing: CUDA events recorded around each kernel group on
+// the launching stream, resolved when the caller asks for the totals.
+struct StageTotal {
+  std::string name;
+  double ms = 0.0;
+  int64_t calls = 0;
+};
+struct PendingStage {
+  int index;
+  cudaEvent_t start, stop;
+};
+struct Profiler {
+  bool on = false;
+  std::vector<StageTotal> totals;
+  std::vector<PendingStage> pending;
+  std::vector<cudaEvent_t> pool;
+};
+
+// Context state (opaque to callers).
+struct Ctx {
+  int device = 0;
+  int sm_count = 0;
+  int async = 0;
+  size_t smem_optin = 0;      // max dynamic shared memory per block (opt-in)
+  uint32_t* d_err = nullptr;  // device error word
+  uint32_t* h_err = nullptr;  // pinned host mirror
+  int64_t launches = 0;       // kernels this context has launched
+  Profiler prof;
+  char last_error[256] = {0};
+};
+
+// Brackets one kernel group with profiling events (no-op when profiling is off).
+class Stage {
+ public:
+  Stage(Ctx* ctx, cudaStream_t s, const char* name);
+  ~Stage();
+ private:
+  Ctx* ctx_;
+  cudaStream_t s_;
+  int index_ = -1;
+  cudaEvent_t start_ = nullptr;
+};
+
+// Count one kernel launch of this context.
+inline void counted(Ctx* ctx, int n = 1) { ctx->launches += n; }
+
+// Bump allocator over a caller workspace; with base == nullptr it only measures.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+  size_t size() const { return (off + 255) & ~size_t(255); }
+};
+
+// ---- workspace layouts ----------------------------------------------------
+
+struct ScanWs {
+  int64_t* block_sums;  // one per scan tile, plus the total
+};
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int64_t kScanTile = kScanThreads * kScanItems;
+inline int64_t scan_tiles(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+inline ScanWs carve_scan(Carver& c, int64_t n) { return ScanWs{c.take<int64_t>(scan_tiles(n) + 2)}; }
+
+struct CountWs {
+  int32_t* big_queue;   // vertices left to the block kernel
+  uint32_t* counters;   // [0] queue length, [1] vertex cursor of the warp kernel, [2..3] spare
+  int64_t* vcount;      // listing: triangles per apex vertex (n)
+  int64_t* voff;        // listing: output offsets (n + 1)
+  ScanWs scan;
+};
+CountWs carve_count(Carver& c, int32_t n, bool listing);
+
+struct OrientWs {
+  int32_t* cursor;      // fill cursor per vertex
+  int32_t* big_queue;   // vertices whose lists the block sorter takes
+  uint32_t* counters;   // [0] queue length
+  ScanWs scan;
+};
+OrientWs carve_orient(Carver& c, int32_t n, int64_t m);
+
+struct SparsifyWs {
+  uint8_t* keep;        // coin per oriented edge (m)
+  int32_t* kept_count;  // kept edges per vertex (n)
+  int64_t* offsets;     // kept CSR offsets (n + 1)
+  int32_t* cols;        // kept CSR columns (m)
+  ScanWs scan;
+  CountWs count;
+};
+SparsifyWs carve_sparsify(Carver& c, int32_t n, int64_t m);
+
+// ---- launchers (stream-ordered, no synchronisation) -------------------------
+
+cudaError_t exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, ScanWs ws, cudaStream_t s);
+cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, ScanWs ws, cudaStream_t s);
+
+cudaError_t launch_orient(Ctx* ctx, int32_t n, int64_t m, const int32_t* edges, int64_t* offsets,
+                          int32_t* cols, int32_t* deg, int32_t* dhat, OrientWs ws, cudaStream_t s);
+
+enum CountMode { MODE_COUNT = 0, MODE_LOCAL = 1, MODE_LIST_COUNT = 2, MODE_LIST_WRITE = 3 };
+
+struct CountArgs {
+  int32_t n;
+  int64_t m;
+  const int64_t* offsets;
+  const int32_t* cols;
+  unsigned long long* total;  // MODE_COUNT / MODE_LOCAL / MODE_LIST_COUNT
+  int64_t* tv;                // MODE_LOCAL
+  int32_t* tri;               // MODE_LIST_WRITE
+  int64_t cap;                // MODE_LIST_WRITE
+};
+cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a, CountWs ws, cudaStream_t s);
+cudaError_t launch_clustering(Ctx* ctx, int32_t n, const int32_t* deg, const int64_t* tv, double* cc, cudaStream_t s);
+
+cudaError_t launch_sparsify(Ctx* ctx, int32_t n, int64_t m, const int64_t* offsets, const int32_t* cols,
+                            uint64_t threshold53, uint64_t seed, SparsifyWs ws, int64_t* kept_edges,
+                            cudaStream_t s);
+
+// Grid of a persistent kernel: resident blocks per SM times the SM count.
+int persistent_blocks(Ctx* ctx, const void* kernel, int threads, size_t dyn_smem);
+
+// ---- device helpers -------------------------------------------------------------
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ void set_err(uint32_t* err, uint32_t bit) { atomicOr(err, bit); }
+
+}  // namespace tc

@@ -1,0 +1,262 @@
+// Orientation by the degree order: the preprocessing of NodeIteratorN
+// (Figure 2): for each edge (u, v) store the later endpoint in the list of the
+// earlier one, where u precedes v iff d_u < d_v, or d_u = d_v and u < v
+// (Eq. (1)); then sort every list N_v ascending.
+//
+// GB300 mapping (all HBM/L2 traffic, no tensor cores):
+//   k_degree        grid-stride over the edge list, 8-byte pair loads, RED.ADD
+//                   into deg[] (4n bytes, L2-resident for n <= 2^25)
+//   k_orient_count  same pass shape, gathers deg[a], deg[b], counts dhat[src]
+//   exclusive scan  offsets = scan(dhat)
+//   k_scatter       third pass: cols[offsets[src] + cursor[src]++] = dst
+//   k_sort_small    one thread per vertex: lists of <= 32 ids sorted in
+//                   registers by a bitonic network sized to the warp's longest
+//                   list; longer lists are queued
+//   k_sort_big      one block per queued list: bitonic sort in shared memory
+// Sorted lists are checked for repeated ids (a repeated edge of the input).
+#include <algorithm>
+#include <climits>
+
+#include "tc_internal.cuh"
+
+namespace tc {
+
+OrientWs carve_orient(Carver& c, int32_t n, int64_t) {
+  OrientWs w;
+  w.cursor = c.take<int32_t>(static_cast<size_t>(n > 0 ? n : 1));
+  w.big_queue = c.take<int32_t>(static_cast<size_t>(n > 0 ? n : 1));
+  w.counters = c.take<uint32_t>(4);
+  w.scan = carve_scan(c, n);
+  return w;
+}
+
+namespace {
+
+__device__ __forceinline__ bool precedes(int32_t da, int32_t a, int32_t db, int32_t b) {
+  return da < db || (da == db && a < b);
+}
+
+__device__ __forceinline__ bool edge_ok(int2 p, int32_t n, uint32_t* err) {
+  if (static_cast<uint32_t>(p.x) >= static_cast<uint32_t>(n) ||
+      static_cast<uint32_t>(p.y) >= static_cast<uint32_t>(n)) {
+    set_err(err, ERR_BAD_ID);
+    return false;
+  }
+  if (p.x == p.y) {
+    set_err(err, ERR_SELF_LOOP);
+    return false;
+  }
+  return true;
+}
+
+__global__ void k_degree(const int2* __restrict__ edges, int64_t m, int32_t n, int32_t* __restrict__ deg,
+                         uint32_t* err) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride) {
+    int2 p = edges[e];
+    if (!edge_ok(p, n, err)) continue;
+    atomicAdd(&deg[p.x], 1);
+    atomicAdd(&deg[p.y], 1);
+  }
+}
+
+__global__ void k_orient_count(const int2* __restrict__ edges, int64_t m, int32_t n,
+                               const int32_t* __restrict__ deg, int32_t* __restrict__ dhat) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride) {
+    int2 p = edges[e];
+    if (static_cast<uint32_t>(p.x) >= static_cast<uint32_t>(n) ||
+        static_cast<uint32_t>(p.y) >= static_cast<uint32_t>(n) || p.x == p.y)
+      continue;
+    int32_t src = precedes(deg[p.x], p.x, deg[p.y], p.y) ? p.x : p.y;
+    atomicAdd(&dhat[src], 1);
+  }
+}
+
+__global__ void k_scatter(const int2* __restrict__ edges, int64_t m, int32_t n, const int32_t* __restrict__ deg,
+                          const int64_t* __restrict__ offsets, int32_t* __restrict__ cursor,
+                          int32_t* __restrict__ cols, uint32_t* err) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride) {
+    int2 p = edges[e];
+    if (static_cast<uint32_t>(p.x) >= static_cast<uint32_t>(n) ||
+        static_cast<uint32_t>(p.y) >= static_cast<uint32_t>(n) || p.x == p.y)
+      continue;
+    bool fwd = precedes(deg[p.x], p.x, deg[p.y], p.y);
+    int32_t src = fwd ? p.x : p.y, dst = fwd ? p.y : p.x;
+    int64_t pos = offsets[src] + atomicAdd(&cursor[src], 1);
+    if (pos < offsets[src + 1]) cols[pos] = dst;
+    else set_err(err, ERR_BAD_CSR);  // unreachable for a consistent count
+  }
+}
+
+// Bitonic sorting network over N registers (ascending), fully unrolled so the
+// array stays in registers.
+template <int N>
+__device__ __forceinline__ void bitonic_regs(int32_t (&a)[N]) {
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          int32_t x = a[i], y = a[l];
+          int32_t lo = min(x, y), hi = max(x, y);
+          a[i] = up ? lo : hi;
+          a[l] = up ? hi : lo;
+        }
+      }
+    }
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void sort_list_regs(int32_t* __restrict__ p, int len, uint32_t* err) {
+  int32_t a[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) a[i] = i < len ? p[i] : INT_MAX;
+  bitonic_regs<N>(a);
+  bool dup = false;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (i < len) p[i] = a[i];
+    if (i > 0 && i < len) dup |= a[i] == a[i - 1];
+  }
+  if (dup) set_err(err, ERR_DUPLICATE);
+}
+
+// One thread per vertex.  The network size is the warp's longest short list
+// rounded up to a power of two, so one warp runs one network.
+__global__ void k_sort_small(int32_t n, const int64_t* __restrict__ offsets, int32_t* __restrict__ cols,
+                             int32_t* __restrict__ big_queue, uint32_t* __restrict__ counters, uint32_t* err) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  // whole warps iterate together so the warp-wide reduction below is legal
+  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < n; base += stride) {
+    const int64_t v = base + threadIdx.x;
+    int len = 0;
+    int64_t beg = 0;
+    if (v < n) {
+      beg = offsets[v];
+      const int64_t l = offsets[v + 1] - beg;
+      if (l > 32) {
+        big_queue[atomicAdd(&counters[0], 1u)] = static_cast<int32_t>(v);
+      } else {
+        len = static_cast<int>(l);
+      }
+    }
+    const int wmax = __reduce_max_sync(FULL, len);
+    int32_t* p = cols + beg;
+    if (wmax <= 1) continue;
+    if (wmax <= 2) sort_list_regs<2>(p, len, err);
+    else if (wmax <= 4) sort_list_regs<4>(p, len, err);
+    else if (wmax <= 8) sort_list_regs<8>(p, len, err);
+    else if (wmax <= 16) sort_list_regs<16>(p, len, err);
+    else sort_list_regs<32>(p, len, err);
+  }
+}
+
+// One block per queued list (33 .. kSortBlockCap ids): bitonic sort in shared memory.
+__global__ void __launch_bounds__(1024) k_sort_big(const int64_t* __restrict__ offsets, int32_t* __restrict__ cols,
+                                                   const int32_t* __restrict__ big_queue,
+                                                   const uint32_t* __restrict__ counters, uint32_t* err) {
+  extern __shared__ int32_t sbuf[];
+  const uint32_t qn = counters[0];
+  for (uint32_t qi = blockIdx.x; qi < qn; qi += gridDim.x) {
+    const int32_t v = big_queue[qi];
+    const int64_t beg = offsets[v];
+    const int64_t len = offsets[v + 1] - beg;
+    if (len > kSortBlockCap) {
+      if (threadIdx.x == 0) set_err(err, ERR_TOO_LONG);
+      continue;
+    }
+    int P = 64;
+    while (P < len) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) sbuf[i] = i < len ? cols[beg + i] : INT_MAX;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+          const int l = i ^ j;
+          if (l > i) {
+            const bool up = (i & k) == 0;
+            int32_t x = sbuf[i], y = sbuf[l];
+            if ((x > y) == up) {
+              sbuf[i] = y;
+              sbuf[l] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    bool dup = false;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      cols[beg + i] = sbuf[i];
+      if (i > 0) dup |= sbuf[i] == sbuf[i - 1];
+    }
+    if (dup) set_err(err, ERR_DUPLICATE);
+    __syncthreads();
+  }
+}
+
+bool g_big_attr_set[64] = {false};
+
+}  // namespace
+
+cudaError_t launch_orient(Ctx* ctx, int32_t n, int64_t m, const int32_t* edges, int64_t* offsets, int32_t* cols,
+                          int32_t* deg, int32_t* dhat, OrientWs ws, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(deg, 0, sizeof(int32_t) * static_cast<size_t>(n), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(dhat, 0, sizeof(int32_t) * static_cast<size_t>(n), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ws.cursor, 0, sizeof(int32_t) * static_cast<size_t>(n), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ws.counters, 0, sizeof(uint32_t) * 4, s)) != cudaSuccess) return e;
+  const int2* ep = reinterpret_cast<const int2*>(edges);
+  const int threads = 512;
+  const int grid_e = static_cast<int>(min64((m + threads - 1) / threads, static_cast<int64_t>(ctx->sm_count) * 8));
+  if (m > 0) {
+    {
+      Stage st(ctx, s, "orient.degree");
+      k_degree<<<grid_e, threads, 0, s>>>(ep, m, n, deg, ctx->d_err);
+    }
+    {
+      Stage st(ctx, s, "orient.orient_count");
+      k_orient_count<<<grid_e, threads, 0, s>>>(ep, m, n, deg, dhat);
+    }
+    counted(ctx, 2);
+  }
+  {
+    Stage st(ctx, s, "orient.scan");
+    if ((e = exclusive_scan_i32(dhat, offsets, n, ws.scan, s)) != cudaSuccess) return e;
+    counted(ctx, n > 0 ? 3 : 1);
+  }
+  if (m > 0) {
+    Stage st(ctx, s, "orient.scatter");
+    k_scatter<<<grid_e, threads, 0, s>>>(ep, m, n, deg, offsets, ws.cursor, cols, ctx->d_err);
+    counted(ctx);
+  }
+  if (n > 0) {
+    const int grid_v = static_cast<int>(min64((n + 255) / 256, static_cast<int64_t>(ctx->sm_count) * 16));
+    {
+      Stage st(ctx, s, "orient.sort_small");
+      k_sort_small<<<grid_v, 256, 0, s>>>(n, offsets, cols, ws.big_queue, ws.counters, ctx->d_err);
+    }
+    const size_t smem = sizeof(int32_t) * kSortBlockCap;
+    if (ctx->device >= 0 && ctx->device < 64 && !g_big_attr_set[ctx->device]) {
+      if ((e = cudaFuncSetAttribute(k_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem))) != cudaSuccess)
+        return e;
+      g_big_attr_set[ctx->device] = true;
+    }
+    {
+      Stage st(ctx, s, "orient.sort_big");
+      k_sort_big<<<ctx->sm_count, 1024, smem, s>>>(offsets, cols, ws.big_queue, ws.counters, ctx->d_err);
+    }
+    counted(ctx, 2);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace tc

@@ -1,0 +1,256 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
+
+Every count here is an exact integer and must match bit for bit; C_v is one
+IEEE division of exact operands on both sides and must match bit for bit too.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests import brute
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tc():
+    from paper_1706_05151_gb300 import build
+    build.build()
+    import paper_1706_05151_gb300 as lib
+    return lib
+
+
+def to_dev(e: np.ndarray) -> torch.Tensor:
+    return torch.from_numpy(np.ascontiguousarray(e, dtype=np.int32)).cuda()
+
+
+def check_orient(tc, n, e, g=None):
+    adj = oracle.Adjacency(n, e)
+    off, cols, dhat = adj.orient()
+    g = g or tc.orient(to_dev(e), n)
+    assert np.array_equal(g.offsets.cpu().numpy(), off)
+    assert np.array_equal(g.cols.cpu().numpy(), cols)
+    assert np.array_equal(g.deg.cpu().numpy(), adj.deg)
+    assert np.array_equal(g.dhat.cpu().numpy(), dhat)
+    return adj, g
+
+
+def check_all(tc, n, e, listing=True):
+    """Orientation, T, T_v, C_v and listing against the oracle."""
+    adj, g = check_orient(tc, n, e)
+    ref = adj.count(local=True, listing=listing)
+    assert tc.count(g) == ref["T"]
+    T, tv, cc = tc.count_local(g)
+    assert T == ref["T"]
+    assert np.array_equal(tv.cpu().numpy(), ref["tv"])
+    ref_cc = oracle.clustering(adj.deg, ref["tv"])
+    assert np.array_equal(cc.cpu().numpy().view(np.uint64), ref_cc.view(np.uint64))
+    if listing:
+        tri = tc.list_triangles(g).cpu().numpy()
+        assert len(tri) == ref["T"]
+        # both sides emit (v, u, w) with v < u < w in the order: compare the row sets
+        a = tri[np.lexsort((tri[:, 2], tri[:, 1], tri[:, 0]))] if len(tri) else tri
+        r = ref["tri"]
+        b = r[np.lexsort((r[:, 2], r[:, 1], r[:, 0]))] if len(r) else r
+        assert np.array_equal(a, b)
+    return g, ref
+
+
+# ---- closed forms and degenerate inputs -------------------------------------------
+
+@pytest.mark.parametrize("n", [3, 4, 5, 17, 40, 300, 700])
+def test_complete(tc, n):
+    g, ref = check_all(tc, n, synth.complete(n), listing=n <= 300)
+    assert ref["T"] == math.comb(n, 3)
+
+
+@pytest.mark.parametrize("make,n", [
+    (lambda: synth.cycle(1000), 1000), (lambda: synth.wheel(3), 4), (lambda: synth.wheel(1000), 1001),
+    (lambda: synth.star(5000), 5001), (lambda: synth.complete_bipartite(40, 60), 100),
+    (lambda: synth.random_tree(20000, 5), 20000),
+])
+def test_closed_forms(tc, make, n):
+    check_all(tc, n, make())
+
+
+def test_empty_graphs(tc):
+    for n in [0, 1, 7]:
+        e = np.zeros((0, 2), np.int32)
+        g = tc.orient(torch.zeros((0, 2), dtype=torch.int32, device="cuda"), n)
+        assert tc.count(g) == 0
+        T, tv, _ = tc.count_local(g)
+        assert T == 0 and (n == 0 or int(tv.abs().sum()) == 0)
+        assert len(tc.list_triangles(g)) == 0
+        assert tc.sparsify_count(g, 0.5, 1)[:2] == (0, 0)
+
+
+def test_single_triangle_with_isolated_vertices(tc):
+    check_all(tc, 10, np.array([[5, 2], [2, 9], [9, 5]], np.int32))
+
+
+# ---- the paper's workload classes at oracle-friendly sizes ----------------------------
+
+def test_erdos_renyi_config(tc):
+    # G(n = 16384, M = 131072 draws): the small single-graph configuration
+    n = 16384
+    check_all(tc, n, synth.er(n, 131072, 1))
+
+
+@pytest.mark.parametrize("n,k,seed", [(1 << 14, 16, 2), (100003, 16, 3), (5000, 40, 4)])
+def test_preferential_attachment(tc, n, k, seed):
+    check_all(tc, n, synth.shuffle_edges(synth.ba(n, k, seed), seed))
+
+
+@pytest.mark.parametrize("scale,ef,seed", [(12, 16, 5), (14, 16, 6), (15, 8, 7)])
+def test_rmat(tc, scale, ef, seed):
+    check_all(tc, 1 << scale, synth.rmat(scale, ef, seed))
+
+
+@pytest.mark.parametrize("n,dbar,seed", [(20000, 48.0, 8), (3000, 64.0, 9)])
+def test_chung_lu(tc, n, dbar, seed):
+    check_all(tc, n, synth.chung_lu(n, dbar, 2.1, seed, 0))
+
+
+def test_dense_graph_uses_block_kernel(tc):
+    # lists longer than the warp kernel's staging (256 ids) go to the block kernel
+    rng = np.random.default_rng(10)
+    n = 900
+    iu = np.triu_indices(n, 1)
+    keep = rng.random(len(iu[0])) < 0.8
+    e = np.stack([iu[0][keep], iu[1][keep]], axis=1).astype(np.int32)
+    g, ref = check_all(tc, n, synth.shuffle_edges(e, 10), listing=False)
+    assert int(g.dhat.max()) > 256
+
+
+def test_chunked_block_kernel_on_large_clique(tc):
+    # K_n with n > 8193: N_v longer than one shared-memory chunk (8192 ids) and
+    # sorted by the block sorter; closed forms T = C(n,3), T_v = C(n-1,2), C_v = 1
+    n = 8300
+    e = synth.shuffle_edges(synth.complete(n), 11)
+    g = tc.orient(to_dev(e), n)
+    assert int(g.dhat.max()) == n - 1
+    off = g.offsets.cpu().numpy()
+    cols = g.cols.cpu().numpy()
+    assert np.all(np.diff(cols[off[0]:off[1]]) > 0)
+    assert tc.count(g) == math.comb(n, 3)
+    T, tv, cc = tc.count_local(g)
+    assert T == math.comb(n, 3)
+    assert torch.all(tv == math.comb(n - 1, 2))
+    assert torch.all(cc == 1.0)
+
+
+# ---- invariants --------------------------------------------------------------------
+
+def test_relabel_and_edge_order_invariance(tc):
+    n = 1 << 13
+    e = synth.rmat(13, 16, 12)
+    perm = np.random.default_rng(12).permutation(n).astype(np.int32)
+    g1 = tc.orient(to_dev(e), n)
+    g2 = tc.orient(to_dev(synth.relabel(e, perm)), n)
+    g3 = tc.orient(to_dev(synth.shuffle_edges(e, 13)), n)
+    T1, tv1, _ = tc.count_local(g1)
+    T2, tv2, _ = tc.count_local(g2)
+    assert T1 == T2
+    assert np.array_equal(tv2.cpu().numpy()[perm], tv1.cpu().numpy())
+    assert torch.equal(g1.offsets, g3.offsets) and torch.equal(g1.cols, g3.cols)
+    assert int(tv1.sum()) == 3 * T1
+
+
+def test_repeated_runs_are_identical(tc):
+    n = 1 << 14
+    g = tc.orient(to_dev(synth.rmat(14, 16, 14)), n)
+    a = tc.count_local(g)
+    b = tc.count_local(g)
+    assert a[0] == b[0] and torch.equal(a[1], b[1])
+    t1 = tc.list_triangles(g)
+    t2 = tc.list_triangles(g)
+    assert t1.shape == t2.shape
+
+
+# ---- sparsification (Section 9.1) -----------------------------------------------------
+
+@pytest.mark.parametrize("q,seed", [(0.1, 1), (0.1, 2), (0.3, 3), (0.5, 4), (1.0, 5), (0.0, 6)])
+def test_sparsify_matches_oracle(tc, q, seed):
+    n = 1 << 14
+    e = synth.rmat(14, 16, 15)
+    g = tc.orient(to_dev(e), n)
+    t, mk, est = tc.sparsify_count(g, q, seed)
+    rt, rmk, rest = oracle.sparsify_count(n, e, seed, q)
+    assert (t, mk) == (rt, rmk)
+    if q > 0:
+        assert est == rest
+
+
+def test_sparsify_q_one_is_exact(tc):
+    n = 1 << 12
+    e = synth.ba(n, 16, 16)
+    g = tc.orient(to_dev(e), n)
+    t, mk, _ = tc.sparsify_count(g, 1.0, 123)
+    assert mk == len(e) and t == tc.count(g)
+
+
+# ---- error handling -----------------------------------------------------------------
+
+def test_invalid_graphs_are_reported(tc):
+    bad = {
+        "self-loop": (np.array([[0, 1], [2, 2]], np.int32), 3),
+        "repeated": (np.array([[0, 1], [1, 0]], np.int32), 3),
+        "out of range": (np.array([[0, 5]], np.int32), 3),
+        "negative": (np.array([[0, -1]], np.int32), 3),
+    }
+    for what, (e, n) in bad.items():
+        with pytest.raises(tc.TcError) as ex:
+            tc.orient(to_dev(e), n)
+        assert ex.value.status == 2, what
+
+
+def test_repeated_edge_in_long_list_is_reported(tc):
+    n = 600
+    e = synth.complete(n)
+    e = np.concatenate([e, e[-1:][:, ::-1]])  # the last edge again, reversed
+    with pytest.raises(tc.TcError) as ex:
+        tc.orient(to_dev(e), n)
+    assert ex.value.status == 2
+
+
+def test_workspace_and_capacity_errors(tc):
+    import ctypes
+    n = 1 << 10
+    g = tc.orient(to_dev(synth.complete(40)), 40)
+    ctx = tc.default_context()
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    total = torch.empty(1, dtype=torch.int64, device="cuda")
+    st = ctx.lib.tc_count(ctx.handle, ctypes.byref(g.struct()), ctypes.c_void_p(total.data_ptr()),
+                          ctypes.c_void_p(small.data_ptr()), 16, None)
+    assert st == 3
+    tri = torch.empty((10, 3), dtype=torch.int32, device="cuda")
+    with pytest.raises(tc.TcError) as ex:
+        tc.list_triangles_into(g, tri)
+    assert ex.value.status == 4
+    big = torch.empty((math.comb(40, 3), 3), dtype=torch.int32, device="cuda")
+    assert tc.list_triangles_into(g, big) == math.comb(40, 3)
+    with pytest.raises(tc.TcError) as ex:
+        tc.sparsify_count(g, 1.5, 0)
+    assert ex.value.status == 1
+    del n
+
+
+def test_broken_csr_is_reported_not_read(tc):
+    # offsets pointing past m must give TC_ERR_INVALID_GRAPH, not an out-of-bounds read
+    off = torch.tensor([0, 2, 50, 3], dtype=torch.int64, device="cuda")
+    cols = torch.tensor([1, 2, 2], dtype=torch.int32, device="cuda")
+    g = tc.graph_from_csr(off, cols)
+    with pytest.raises(tc.TcError) as ex:
+        tc.count(g)
+    assert ex.value.status == 2
+    cols_bad = torch.tensor([1, 7, 2], dtype=torch.int32, device="cuda")
+    g2 = tc.graph_from_csr(torch.tensor([0, 2, 3, 3], dtype=torch.int64, device="cuda"), cols_bad)
+    with pytest.raises(tc.TcError) as ex:
+        tc.count(g2)
+    assert ex.value.status == 2
