@@ -280,7 +280,8 @@ static tc_status count_impl(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev,
   if (st != TC_OK) return st;
   if (!total_dev) return fail(ctx, TC_ERR_INVALID_ARG, "total_dev is NULL");
   const bool local = tv_dev != nullptr;
-  if (cc_dev && (!local || !g->deg)) return fail(ctx, TC_ERR_INVALID_ARG, "clustering needs tv_dev and g->deg");
+  if (cc_dev && (!local || (g->n > 0 && !g->deg)))
+    return fail(ctx, TC_ERR_INVALID_ARG, "clustering needs tv_dev and g->deg");
   if ((st = check_ws(ctx, TC_OP_COUNT, g->n, g->m, ws, ws_bytes)) != TC_OK) return st;
   if ((st = begin(ctx, s)) != TC_OK) return st;
   Carver c(ws);
