@@ -3,9 +3,8 @@
 
 One step = the whole hot path over one synthetic graph already resident in
 HBM: orientation by the degree order (tc_orient), exact count with per-vertex
-counts and clustering coefficients (tc_count_local), two-pass listing
-(tc_list_count + tc_list_write) and edge sparsification at q = 0.1
-(tc_sparsify_count).  The metric is oriented edges per second (m per step),
+counts, clustering coefficients and the two-pass triangle list (tc_analyze),
+and edge sparsification at q = 0.1 (tc_sparsify_count).  The metric is oriented edges per second (m per step),
 with the intersection kernel's achieved fraction of the measured HBM roofline.
 
 Default workload: preferential attachment PA(n = 2^24, 16 edges per new
@@ -42,6 +41,8 @@ WORKLOADS = {
     "ba27": dict(kind="ba", n=1 << 27, k=16, label="preferential attachment PA(n=2^27, k=16)"),
     "rmat24": dict(kind="rmat", scale=24, ef=16, label="R-MAT scale 24, edge factor 16 (0.57/0.19/0.19/0.05)"),
     "er": dict(kind="er", n=16384, draws=131072, label="Erdos-Renyi G(n=16384, M=131072 draws)"),
+    "ba22": dict(kind="ba", n=1 << 22, k=16, label="preferential attachment PA(n=2^22, k=16)"),
+    "rmat22": dict(kind="rmat", scale=22, ef=16, label="R-MAT scale 22, edge factor 16 (0.57/0.19/0.19/0.05)"),
 }
 
 
@@ -227,10 +228,12 @@ def main():
     edges_dev = edges_host.to(dev)
     q, seed = args.q, args.seed
 
+    tri_buf = [None]
+
     def step():
         g = tc.orient(edges_dev, n, ctx)
-        T, tv, cc = tc.count_local(g, True, ctx)
-        tri = tc.list_triangles(g, ctx)
+        T, tv, cc, tri = tc.analyze(g, True, tri_buf[0], ctx)
+        tri_buf[0] = tri if tri_buf[0] is None or len(tri) > tri_buf[0].shape[0] else tri_buf[0]
         sp = tc.sparsify_count(g, q, seed, ctx)
         return g, T, tv, cc, tri, sp
 
@@ -290,8 +293,7 @@ def main():
     for _ in range(args.e2e_steps):
         ed = edges_host.to(dev, non_blocking=True)
         g2 = tc.orient(ed, n, ctx)
-        T2, tv2, cc2 = tc.count_local(g2, True, ctx)
-        tri2 = tc.list_triangles(g2, ctx)
+        T2, tv2, cc2, tri2 = tc.analyze(g2, True, tri_buf[0], ctx)
         sp2 = tc.sparsify_count(g2, q, seed, ctx)
         tv_host.copy_(tv2, non_blocking=True)
         cc_host.copy_(cc2, non_blocking=True)
@@ -312,12 +314,12 @@ def main():
 
     # ---- roofline of the intersection kernel (per-vertex counting pass) ----
     peak, peak_src = load_peaks()
-    inter_ms = sum(stages.get(k, (0.0, 0))[0] for k in ("local.warp", "local.block"))
-    inter_calls = max(stages.get("local.warp", (0.0, 0))[1], 1)
+    inter_ms = sum(stages.get(k, (0.0, 0))[0] for k in ("local.tile", "local.block"))
+    inter_calls = max(stages.get("local.tile", (0.0, 0))[1], 1)
     inter_avg_ms = inter_ms / inter_calls
     b_alg = 4 * W + 4 * m + 8 * (n + 1)
     achieved = b_alg / (inter_avg_ms * 1e-3) / 1e9
-    traffic = recorded_traffic("local.warp", args.workload)
+    traffic = recorded_traffic("local.tile", args.workload)
 
     if rank == 0:
         cpu = None
@@ -337,13 +339,13 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": w["label"], "n": n, "m": m, "triangles": T, "W_sum_d_dhat": W,
                        "q": q, "seed": args.seed,
-                       "step": "tc_orient + tc_count_local(C_v) + tc_list + tc_sparsify_count(q)",
+                       "step": "tc_orient + tc_analyze(T, T_v, C_v, triangle list) + tc_sparsify_count(q)",
                        "l2": "inputs larger than L2 (edge list %.2f GB, CSR %.2f GB)" % (
                            8 * m / 1e9, (4 * m + 8 * n) / 1e9),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_count_warp+k_count_block (tc_count_local)",
+                         "kernel": "k_count_tile+k_count_block, per-vertex pass of tc_analyze",
                          "algorithmic_bytes": b_alg, "avg_launch_ms": inter_avg_ms, "peak_source": peak_src},
             "e2e": {"value": m_total / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},

@@ -57,7 +57,7 @@ typedef enum {
 typedef enum {
   TC_OP_ORIENT = 0,
   TC_OP_COUNT = 1,       /* tc_count and tc_count_local */
-  TC_OP_LIST = 2,        /* tc_list, tc_list_count, tc_list_write */
+  TC_OP_LIST = 2,        /* tc_list, tc_list_count, tc_list_write, tc_analyze */
   TC_OP_SPARSIFY = 3     /* tc_sparsify_count */
 } tc_op;
 
@@ -187,6 +187,22 @@ tc_status tc_list_write(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_
  */
 tc_status tc_list(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_t cap, int64_t* count_out,
                   void* ws, size_t ws_bytes, tc_stream stream);
+
+/*
+ * T, per-vertex counts, clustering coefficients and the triangle list in two
+ * passes of the intersection instead of three: pass 1 computes T, T_v
+ * (Section 11) and the triangles of each apex vertex; C_v follows
+ * (Preliminaries); a scan turns the apex counts into output positions; pass 2
+ * writes the triples as tc_list_write does (Section 10).  Waits after pass 1
+ * (even in async mode) to check the total against cap.
+ *   total_dev device uint64[1]; tv_dev device int64[n]; cc_dev device double[n]
+ *   or NULL (needs g->deg); tri_dev device int32[cap][3]; *count_out (host)
+ *   receives T.  With TC_ERR_CAPACITY, T, T_v and C_v are complete, *count_out
+ *   holds the capacity needed and no triple was written.  Workspace: TC_OP_LIST.
+ */
+tc_status tc_analyze(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, int64_t* tv_dev, double* cc_dev,
+                     int32_t* tri_dev, int64_t cap, int64_t* count_out, void* ws, size_t ws_bytes,
+                     tc_stream stream);
 
 /* ---- sparsification (Section 9.1, Figure "sparsification") ---------------- */
 

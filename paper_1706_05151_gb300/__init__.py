@@ -33,7 +33,7 @@ STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_INVALID_GRAPH", 3: "TC
 # every symbol include/tc.h declares
 EXPORTS = ["tc_ctx_create", "tc_ctx_destroy", "tc_ctx_set_async", "tc_ctx_status", "tc_status_string",
            "tc_last_error", "tc_ctx_sm_count", "tc_version", "tc_workspace_size", "tc_orient", "tc_count",
-           "tc_count_local", "tc_list_count", "tc_list_write", "tc_list", "tc_sparsify_count",
+           "tc_count_local", "tc_list_count", "tc_list_write", "tc_list", "tc_analyze", "tc_sparsify_count",
            "tc_ctx_set_profiling", "tc_ctx_stage_count", "tc_ctx_stage", "tc_ctx_reset_stats", "tc_ctx_launches"]
 
 
@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH):
             "tc_list_count": (i32, [vp, G, vp, vp, sz, vp]),
             "tc_list_write": (i32, [vp, G, vp, i64, vp, sz, vp]),
             "tc_list": (i32, [vp, G, vp, i64, ctypes.POINTER(i64), vp, sz, vp]),
+            "tc_analyze": (i32, [vp, G, vp, vp, vp, vp, i64, ctypes.POINTER(i64), vp, sz, vp]),
             "tc_sparsify_count": (i32, [vp, G, ctypes.c_double, u64, vp, vp, vp, sz, vp]),
             "tc_ctx_set_profiling": (i32, [vp, ctypes.c_int]),
             "tc_ctx_stage_count": (ctypes.c_int, [vp]),
@@ -266,6 +267,34 @@ def list_triangles_into(g: Graph, tri: torch.Tensor, ctx: Context | None = None)
     ctx.check(ctx.lib.tc_list(ctx.handle, ctypes.byref(g.struct()), _ptr(tri), int(tri.shape[0]),
                               ctypes.byref(cnt), _ptr(ws), ws.numel(), _stream(ctx.device)))
     return int(cnt.value)
+
+
+def analyze(g: Graph, clustering: bool = True, tri: torch.Tensor | None = None, ctx: Context | None = None):
+    """tc_analyze: (T, T_v int64[n], C_v float64[n] or None, triples int32[T, 3]).
+
+    `tri` is an optional int32[cap, 3] output buffer; if it is too small (or
+    absent) the call is repeated once with a buffer of exactly T rows.
+    """
+    ctx = ctx or default_context()
+    total = torch.empty(1, dtype=torch.int64, device=ctx.device)
+    tv = torch.empty(max(g.n, 1), dtype=torch.int64, device=ctx.device)
+    cc = torch.empty(max(g.n, 1), dtype=torch.float64, device=ctx.device) if clustering else None
+    ws = ctx.workspace(TC_OP_LIST, g.n, g.m)
+    gs = g.struct()
+    if tri is None:
+        tri = torch.empty((1, 3), dtype=torch.int32, device=ctx.device)
+    cnt = i64(0)
+
+    def call(buf):
+        return ctx.lib.tc_analyze(ctx.handle, ctypes.byref(gs), _ptr(total), _ptr(tv), _ptr(cc), _ptr(buf),
+                                  int(buf.shape[0]), ctypes.byref(cnt), _ptr(ws), ws.numel(), _stream(ctx.device))
+    st = call(tri)
+    if st == 4:
+        tri = torch.empty((max(int(cnt.value), 1), 3), dtype=torch.int32, device=ctx.device)
+        st = call(tri)
+    ctx.check(st)
+    T = int(cnt.value)
+    return T, tv[: g.n], (cc[: g.n] if cc is not None else None), tri[:T]
 
 
 def sparsify_count(g: Graph, q: float, seed: int, ctx: Context | None = None):

@@ -371,6 +371,51 @@ tc_status tc_list(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_t cap,
   return tc_list_write(ctx, g, tri_dev, cap, ws, ws_bytes, stream);
 }
 
+tc_status tc_analyze(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, int64_t* tv_dev, double* cc_dev,
+                     int32_t* tri_dev, int64_t cap, int64_t* count_out, void* ws, size_t ws_bytes, tc_stream stream) {
+  tc_status st = check_graph(ctx, g);
+  if (st != TC_OK) return st;
+  if (!total_dev || !tv_dev || !count_out) return fail(ctx, TC_ERR_INVALID_ARG, "NULL output");
+  if (cc_dev && g->n > 0 && !g->deg) return fail(ctx, TC_ERR_INVALID_ARG, "clustering needs g->deg");
+  if (cap < 0 || (cap > 0 && !tri_dev)) return fail(ctx, TC_ERR_INVALID_ARG, "bad output buffer");
+  if ((st = check_ws(ctx, TC_OP_LIST, g->n, g->m, ws, ws_bytes)) != TC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = begin(ctx, s)) != TC_OK) return st;
+  Carver c(ws);
+  tc::CountWs w = tc::carve_count(c, g->n, true);
+  cudaError_t e = cudaMemsetAsync(total_dev, 0, sizeof(uint64_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tv_dev, 0, sizeof(int64_t) * static_cast<size_t>(g->n), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.vcount, 0, sizeof(int64_t) * (static_cast<size_t>(g->n) + 1), s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "clear outputs");
+  // pass 1: T, T_v and the triangles of each apex vertex (into w.vcount)
+  tc::CountArgs a{g->n, g->m, g->offsets, g->cols, reinterpret_cast<unsigned long long*>(total_dev), tv_dev,
+                  nullptr, 0};
+  e = tc::launch_count(ctx, tc::MODE_LOCAL, a, w, s);
+  if (e == cudaSuccess && cc_dev) e = tc::launch_clustering(ctx, g->n, g->deg, tv_dev, cc_dev, s);
+  if (e == cudaSuccess) {
+    tc::Stage stg(ctx, s, "analyze.scan");
+    e = tc::exclusive_scan_i64(w.vcount, w.voff, g->n, w.scan, s);
+    tc::counted(ctx, g->n > 0 ? 3 : 1);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "launch");
+  // the total decides whether the triples fit: wait for it (and for the checks)
+  int64_t total = 0;
+  e = cudaMemcpyAsync(&total, w.voff + g->n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "read listing total");
+  if (!ctx->async && (st = status_from_bits(ctx, *ctx->h_err)) != TC_OK) return st;
+  *count_out = total;
+  if (total > cap) return fail(ctx, TC_ERR_CAPACITY, "listing needs %lld triples, capacity %lld",
+                               static_cast<long long>(total), static_cast<long long>(cap));
+  // pass 2: write the triples
+  a.total = nullptr;
+  a.tv = nullptr;
+  a.tri = tri_dev;
+  a.cap = cap;
+  return finish(ctx, s, tc::launch_count(ctx, tc::MODE_LIST_WRITE, a, w, s));
+}
+
 tc_status tc_sparsify_count(tc_ctx* ctx, const tc_graph* g, double q, uint64_t seed, uint64_t* kept_tri_dev,
                             int64_t* kept_edges_dev, void* ws, size_t ws_bytes, tc_stream stream) {
   tc_status st = check_graph(ctx, g);

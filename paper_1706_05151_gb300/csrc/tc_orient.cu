@@ -49,44 +49,95 @@ __device__ __forceinline__ bool edge_ok(int2 p, int32_t n, uint32_t* err) {
   return true;
 }
 
+// Runs of equal keys in consecutive lanes (the usual case for an edge list in
+// adjacency-list order, where one endpoint repeats) are combined so that one
+// lane per run does the atomic.  Returns the run length at the run's first
+// lane and 0 elsewhere; *head_lane receives the first lane of this lane's run.
+__device__ __forceinline__ int run_length(int32_t key, bool valid, int* head_lane) {
+  const int lane = lane_id();
+  const int32_t prev = __shfl_up_sync(FULL, key, 1);
+  const bool pvalid = __shfl_up_sync(FULL, valid, 1);
+  const bool head = lane == 0 || key != prev || valid != pvalid;
+  const unsigned heads = __ballot_sync(FULL, head);
+  *head_lane = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+  if (!head || !valid) return 0;
+  const unsigned after = heads & ~(0xffffffffu >> (31 - lane));
+  const int end = after ? __ffs(after) - 1 : 32;
+  return end - lane;
+}
+
+// Warp-strided edge loop: every lane of a warp runs the same iterations.
+#define FOR_EDGES(e, m)                                                                            \
+  for (int64_t e##0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) & ~int64_t(31); \
+       e##0 < (m); e##0 += static_cast<int64_t>(gridDim.x) * blockDim.x)
+
 __global__ void k_degree(const int2* __restrict__ edges, int64_t m, int32_t n, int32_t* __restrict__ deg,
                          uint32_t* err) {
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride) {
-    int2 p = edges[e];
-    if (!edge_ok(p, n, err)) continue;
-    atomicAdd(&deg[p.x], 1);
-    atomicAdd(&deg[p.y], 1);
+  FOR_EDGES(e, m) {
+    const int64_t e = e0 + lane_id();
+    int2 p = make_int2(0, 0);
+    bool ok = false;
+    if (e < m) {
+      p = edges[e];
+      ok = edge_ok(p, n, err);
+    }
+    int hl;
+    const int cx = run_length(p.x, ok, &hl);
+    if (cx) atomicAdd(&deg[p.x], cx);
+    const int cy = run_length(p.y, ok, &hl);
+    if (cy) atomicAdd(&deg[p.y], cy);
   }
+}
+
+__device__ __forceinline__ bool edge_valid(int2 p, int32_t n) {
+  return static_cast<uint32_t>(p.x) < static_cast<uint32_t>(n) && static_cast<uint32_t>(p.y) < static_cast<uint32_t>(n) &&
+         p.x != p.y;
 }
 
 __global__ void k_orient_count(const int2* __restrict__ edges, int64_t m, int32_t n,
                                const int32_t* __restrict__ deg, int32_t* __restrict__ dhat) {
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride) {
-    int2 p = edges[e];
-    if (static_cast<uint32_t>(p.x) >= static_cast<uint32_t>(n) ||
-        static_cast<uint32_t>(p.y) >= static_cast<uint32_t>(n) || p.x == p.y)
-      continue;
-    int32_t src = precedes(deg[p.x], p.x, deg[p.y], p.y) ? p.x : p.y;
-    atomicAdd(&dhat[src], 1);
+  FOR_EDGES(e, m) {
+    const int64_t e = e0 + lane_id();
+    int32_t src = 0;
+    bool ok = false;
+    if (e < m) {
+      const int2 p = edges[e];
+      ok = edge_valid(p, n);
+      if (ok) src = precedes(deg[p.x], p.x, deg[p.y], p.y) ? p.x : p.y;
+    }
+    int hl;
+    const int c = run_length(src, ok, &hl);
+    if (c) atomicAdd(&dhat[src], c);
   }
 }
 
 __global__ void k_scatter(const int2* __restrict__ edges, int64_t m, int32_t n, const int32_t* __restrict__ deg,
                           const int64_t* __restrict__ offsets, int32_t* __restrict__ cursor,
                           int32_t* __restrict__ cols, uint32_t* err) {
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < m; e += stride) {
-    int2 p = edges[e];
-    if (static_cast<uint32_t>(p.x) >= static_cast<uint32_t>(n) ||
-        static_cast<uint32_t>(p.y) >= static_cast<uint32_t>(n) || p.x == p.y)
-      continue;
-    bool fwd = precedes(deg[p.x], p.x, deg[p.y], p.y);
-    int32_t src = fwd ? p.x : p.y, dst = fwd ? p.y : p.x;
-    int64_t pos = offsets[src] + atomicAdd(&cursor[src], 1);
-    if (pos < offsets[src + 1]) cols[pos] = dst;
-    else set_err(err, ERR_BAD_CSR);  // unreachable for a consistent count
+  FOR_EDGES(e, m) {
+    const int lane = lane_id();
+    const int64_t e = e0 + lane;
+    int32_t src = 0, dst = 0;
+    bool ok = false;
+    if (e < m) {
+      const int2 p = edges[e];
+      ok = edge_valid(p, n);
+      if (ok) {
+        const bool fwd = precedes(deg[p.x], p.x, deg[p.y], p.y);
+        src = fwd ? p.x : p.y;
+        dst = fwd ? p.y : p.x;
+      }
+    }
+    int hl;
+    const int c = run_length(src, ok, &hl);
+    int64_t base = 0;
+    if (c) base = offsets[src] + atomicAdd(&cursor[src], c);
+    base = __shfl_sync(FULL, base, hl);
+    if (ok) {
+      const int64_t pos = base + (lane - hl);
+      if (pos < offsets[src + 1]) cols[pos] = dst;
+      else set_err(err, ERR_BAD_CSR);  // unreachable for a consistent count
+    }
   }
 }
 

@@ -51,8 +51,14 @@ def check_all(tc, n, e, listing=True):
     assert np.array_equal(tv.cpu().numpy(), ref["tv"])
     ref_cc = oracle.clustering(adj.deg, ref["tv"])
     assert np.array_equal(cc.cpu().numpy().view(np.uint64), ref_cc.view(np.uint64))
+    T2, tv2, cc2, tri2 = tc.analyze(g)
+    assert T2 == ref["T"]
+    assert np.array_equal(tv2.cpu().numpy(), ref["tv"])
+    assert np.array_equal(cc2.cpu().numpy().view(np.uint64), ref_cc.view(np.uint64))
+    assert len(tri2) == ref["T"]
     if listing:
         tri = tc.list_triangles(g).cpu().numpy()
+        assert np.array_equal(tri, tri2.cpu().numpy())  # same deterministic order
         assert len(tri) == ref["T"]
         # both sides emit (v, u, w) with v < u < w in the order: compare the row sets
         a = tri[np.lexsort((tri[:, 2], tri[:, 1], tri[:, 0]))] if len(tri) else tri
