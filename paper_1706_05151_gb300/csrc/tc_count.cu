@@ -33,11 +33,15 @@ namespace tc {
 
 namespace {
 
-constexpr int kTile = 512;       // ids staged per warp; longer lists go to the block kernel
-constexpr int kTileWarps = 8;    // warps per block, tile kernel
-constexpr int kUnroll = 4;       // candidate windows in flight per lane
-constexpr int kBlockCap = 8192;  // ids of N_v staged per pass, block kernel
-constexpr int kBlockWarps = 8;   // warps per block, block kernel
+constexpr int kTile = 512;           // ids staged per warp; longer lists go to the block kernel
+constexpr int kTileWarps = 4;        // warps per block, tile kernel
+constexpr int kTileBitsLog2 = 14;    // filter bits per tile (2 KB): <= 512 / 16384 false positives
+constexpr int kUnroll = 4;           // candidate windows in flight per lane
+constexpr int kShortLen = 32;        // N_u shorter than this is walked end to end with others
+constexpr int kOwnCap = 32 * kShortLen;
+constexpr int kBlockCap = 4096;      // ids of N_v staged per pass, block kernel
+constexpr int kBlockBitsLog2 = 16;   // filter bits per staged chunk (8 KB)
+constexpr int kBlockWarps = 8;       // warps per block, block kernel
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
 
@@ -100,116 +104,234 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x) {
 }
 
 // ---------------------------------------------------------------------------
-// Tile kernel
+// Shared batch machinery.  A batch is up to 32 oriented edges (v, u), one per
+// lane.  Short lists N_u (< kShortLen ids) are laid end to end and walked in
+// 32-wide windows (an owner table maps a position to its edge); long lists are
+// walked one edge at a time.  Every candidate w first meets a bitmap filter of
+// the staged lists (one shared load and a bit test); the few that pass (true
+// matches and about S / 2^bits false positives) are queued and checked exactly,
+// 32 at a time, by binary search in the staged N_v.
 // ---------------------------------------------------------------------------
 
-struct EdgeBatch {     // one batch of up to 32 oriented edges (v, u) of a tile
-  int64_t beg[32];     // start of N_u minus the edge's offset in the flattened batch
-  int32_t exc[32];     // exclusive prefix of |N_u| over the batch
+// Multiplicative hash of (salt, id) onto a 2^LOG2-bit filter.
+template <int LOG2>
+__device__ __forceinline__ uint32_t fbit(int32_t w, int32_t salt) {
+  return ((static_cast<uint32_t>(w) ^ (static_cast<uint32_t>(salt) << 26)) * 0x9E3779B1u) >> (32 - LOG2);
+}
+
+template <int LOG2>
+__device__ __forceinline__ bool ftest(const uint32_t* bits, int32_t w, int32_t salt) {
+  const uint32_t h = fbit<LOG2>(w, salt);
+  return (bits[h >> 5] >> (h & 31)) & 1u;
+}
+
+template <int LOG2>
+__device__ __forceinline__ void fset(uint32_t* bits, int32_t w, int32_t salt) {
+  const uint32_t h = fbit<LOG2>(w, salt);
+  atomicOr(&bits[h >> 5], 1u << (h & 31));
+}
+
+struct BatchSmem {
+  int64_t beg[32];        // short list: start of N_u minus its flattened offset; long list: start of N_u
   int32_t u[32];
-  int32_t lo[32];      // N_v's slice of the tile: [lo, lo + len)
+  int32_t lo[32];         // tile kernel: N_v's slice [lo, lo + len) of the tile
   int32_t len[32];
-  int32_t vl[32];      // chunk lane of v
-  uint32_t cnt[32];    // matches of the edge
+  int32_t salt[32];       // filter salt: chunk lane of v (tile kernel), 0 (block kernel)
+  uint32_t cnt[32];       // matches of the edge
+  int32_t qw[64];         // filter survivors: candidate id ...
+  int32_t qs[64];         // ... and its edge
+  uint8_t own[kOwnCap];   // flattened position -> edge, short lists
 };
 
-struct TileSmem {
-  int32_t tile[kTile];
-  int32_t vlo[32];     // tile start of each chunk lane's list (-1 before the group, > S after)
-  uint32_t vcnt[32];   // triangles with apex v (chunk lane)
-  int32_t vrun[32];    // listing: triples written so far per chunk lane
-  EdgeBatch eb;
+struct Probe {            // what the candidates are tested against
+  const int32_t* sv;      // tile kernel: the tile; block kernel: the staged chunk of N_v
+  const uint32_t* bits;   // filter of sv
+  int top;                // binary-search span (power of two)
+  int len;                // block kernel: chunk length
+  int32_t lo, hi;         // block kernel: id range of the chunk
 };
 
-template <int MODE>
-__device__ __forceinline__ void tile_edge_batch(TileSmem& sm, int t0, int S, int top, int32_t glen, int32_t vbase,
-                                                const CountArgs& a, const CountWs& ws, uint32_t* err) {
+template <bool TILE>
+__device__ __forceinline__ bool passes(const Probe& pr, int32_t salt, int32_t w) {
+  if (TILE) return ftest<kTileBitsLog2>(pr.bits, w, salt);
+  return w >= pr.lo && w <= pr.hi && ftest<kBlockBitsLog2>(pr.bits, w, 0);
+}
+
+// Exact check of the first `cnt` queued survivors, with the per-mode effects.
+template <int MODE, bool TILE>
+__device__ __forceinline__ void exact_flush(BatchSmem& bs, const Probe& pr, int cnt, int32_t vbase_or_v, int32_t* vrun,
+                                            unsigned long long* cursor, const CountArgs& a, const CountWs& ws,
+                                            uint32_t* err) {
   const int lane = lane_id();
-  EdgeBatch& eb = sm.eb;
-  const int t = t0 + lane;
-  const bool act = t < S;
-  int vl = 0;
-  int32_t u = 0, len = 0;
-  int64_t ub = 0;
-  if (act) {
-    vl = search32(sm.vlo, static_cast<int32_t>(t));
-    u = sm.tile[t];
-    len = list_bounds(a, u, ub, err);
+  __syncwarp();
+  const bool has = lane < cnt;
+  const int s = has ? bs.qs[lane] : 0;
+  const int32_t w = has ? bs.qw[lane] : 0;
+  bool f = false;
+  if (has) f = TILE ? member(pr.sv + bs.lo[s], bs.len[s], pr.top, w) : member(pr.sv, pr.len, pr.top, w);
+  if (f) {
+    atomicAdd(&bs.cnt[s], 1u);
+    if (MODE == MODE_LOCAL) atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + w), 1ull);
   }
-  const int32_t vlen = __shfl_sync(FULL, glen, vl);
-  const int32_t incl = warp_incl_scan(len);
-  const int32_t tot = __shfl_sync(FULL, incl, 31);
-  const int32_t excl = incl - len;
-  __syncwarp();
-  eb.beg[lane] = ub - excl;
-  eb.exc[lane] = excl;
-  eb.u[lane] = u;
-  eb.vl[lane] = vl;
-  eb.lo[lane] = sm.vlo[vl];
-  eb.len[lane] = vlen;
-  eb.cnt[lane] = 0;
-  __syncwarp();
-
-  for (int32_t p0 = 0; p0 < tot; p0 += 32 * kUnroll) {
-    int32_t w[kUnroll];
-    int s[kUnroll];
-    bool f[kUnroll];
-#pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
-      const int32_t p = p0 + 32 * k + lane;
-      s[k] = 0;
-      w[k] = -1;
-      if (p < tot) {
-        s[k] = search32(eb.exc, p);
-        w[k] = a.cols[eb.beg[s[k]] + p];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
-      const int32_t p = p0 + 32 * k + lane;
-      f[k] = p < tot && member(sm.tile + eb.lo[s[k]], eb.len[s[k]], top, w[k]);
-      if (f[k]) {
-        atomicAdd(&eb.cnt[s[k]], 1u);
-        if (MODE == MODE_LOCAL) atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + w[k]), 1ull);
-      }
-    }
-    if (MODE == MODE_LIST_WRITE) {
-#pragma unroll
-      for (int k = 0; k < kUnroll; ++k) {
-        const unsigned fm = __ballot_sync(FULL, f[k]);
-        if (!fm) continue;
-        const int32_t p = p0 + 32 * k + lane;
-        const int key = p < tot ? eb.vl[s[k]] : 32 + lane;
-        const unsigned same = __match_any_sync(FULL, key);
-        if (f[k]) {
-          const int vlk = eb.vl[s[k]];
-          const int32_t v = vbase + vlk;
-          const int64_t idx = ws.voff[v] + sm.vrun[vlk] + __popc(fm & same & lanemask_lt());
+  if (MODE == MODE_LIST_WRITE) {
+    const unsigned fm = __ballot_sync(FULL, f);
+    if (fm) {
+      if (TILE) {
+        // triples of one apex vertex are written in queue order at voff[v] + running count
+        const int vl = bs.salt[s];
+        const unsigned same = __match_any_sync(FULL, has ? vl : 32 + lane);
+        if (f) {
+          const int32_t v = vbase_or_v + vl;
+          const int64_t idx = ws.voff[v] + vrun[vl] + __popc(fm & same & lanemask_lt());
           if (idx < a.cap) {
             a.tri[3 * idx] = v;
-            a.tri[3 * idx + 1] = eb.u[s[k]];
-            a.tri[3 * idx + 2] = w[k];
+            a.tri[3 * idx + 1] = bs.u[s];
+            a.tri[3 * idx + 2] = w;
           } else {
             set_err(err, ERR_CAPACITY);
           }
         }
         __syncwarp();
-        if (p < tot && lane == 31 - __clz(same)) sm.vrun[eb.vl[s[k]]] += __popc(fm & same);
-        __syncwarp();
+        if (has && lane == 31 - __clz(same)) vrun[vl] += __popc(fm & same);
+      } else {
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(cursor, static_cast<unsigned long long>(__popc(fm)));
+        const int64_t base = static_cast<int64_t>(__shfl_sync(FULL, b0, 0));
+        if (f) {
+          const int64_t idx = base + __popc(fm & lanemask_lt());
+          if (idx < a.cap) {
+            a.tri[3 * idx] = vbase_or_v;
+            a.tri[3 * idx + 1] = bs.u[s];
+            a.tri[3 * idx + 2] = w;
+          } else {
+            set_err(err, ERR_CAPACITY);
+          }
+        }
       }
     }
   }
   __syncwarp();
-  if (act) {
-    const uint32_t c = eb.cnt[lane];
-    if (c) {
-      if (MODE == MODE_LOCAL)
-        atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + u), static_cast<unsigned long long>(c));
-      atomicAdd(&sm.vcnt[vl], c);
+}
+
+// Queue this window's survivors; check 32 of them once 32 are waiting.
+template <int MODE, bool TILE>
+__device__ __forceinline__ void push(BatchSmem& bs, const Probe& pr, bool pass, int32_t w, int s, int& qn,
+                                     int32_t vbase_or_v, int32_t* vrun, unsigned long long* cursor,
+                                     const CountArgs& a, const CountWs& ws, uint32_t* err) {
+  const int lane = lane_id();
+  const unsigned m = __ballot_sync(FULL, pass);
+  if (!m) return;
+  if (pass) {
+    const int pos = qn + __popc(m & lanemask_lt());
+    bs.qw[pos] = w;
+    bs.qs[pos] = s;
+  }
+  qn += __popc(m);
+  if (qn >= 32) {
+    exact_flush<MODE, TILE>(bs, pr, 32, vbase_or_v, vrun, cursor, a, ws, err);
+    const int rest = qn - 32;
+    int32_t tw = 0, ts = 0;
+    if (lane < rest) {
+      tw = bs.qw[32 + lane];
+      ts = bs.qs[32 + lane];
+    }
+    __syncwarp();
+    if (lane < rest) {
+      bs.qw[lane] = tw;
+      bs.qs[lane] = ts;
+    }
+    __syncwarp();
+    qn = rest;
+  }
+}
+
+// One batch of edges (v, u): u on this lane if `act`.  Returns the matches of
+// this lane's edge.  salt/lo/vlen describe this lane's N_v (tile kernel).
+template <int MODE, bool TILE>
+__device__ __forceinline__ uint32_t process_batch(BatchSmem& bs, const Probe& pr, int32_t u, bool act, int32_t salt,
+                                                  int32_t lo, int32_t vlen, int32_t vbase_or_v, int32_t* vrun,
+                                                  unsigned long long* cursor, const CountArgs& a,
+                                                  const CountWs& ws, uint32_t* err) {
+  const int lane = lane_id();
+  int64_t ub = 0;
+  int32_t len = 0;
+  if (act) len = list_bounds(a, u, ub, err);
+  const bool is_short = len < kShortLen;
+  const int32_t slen = is_short ? len : 0;
+  const int32_t incl = warp_incl_scan(slen);
+  const int32_t tot = __shfl_sync(FULL, incl, 31);
+  const int32_t excl = incl - slen;
+  __syncwarp();
+  bs.beg[lane] = is_short ? ub - excl : ub;
+  bs.u[lane] = u;
+  bs.lo[lane] = lo;
+  bs.len[lane] = vlen;
+  bs.salt[lane] = salt;
+  bs.cnt[lane] = 0;
+  for (int i = 0; i < slen; ++i) bs.own[excl + i] = static_cast<uint8_t>(lane);
+  __syncwarp();
+  int qn = 0;
+  // short lists, end to end
+  for (int32_t p0 = 0; p0 < tot; p0 += 32 * kUnroll) {
+    int32_t w[kUnroll];
+    int s[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      const int32_t p = p0 + 32 * k + lane;
+      s[k] = 0;
+      w[k] = 0;
+      if (p < tot) {
+        s[k] = bs.own[p];
+        w[k] = a.cols[bs.beg[s[k]] + p];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      const int32_t p = p0 + 32 * k + lane;
+      const bool pass = p < tot && passes<TILE>(pr, bs.salt[s[k]], w[k]);
+      push<MODE, TILE>(bs, pr, pass, w[k], s[k], qn, vbase_or_v, vrun, cursor, a, ws, err);
     }
   }
+  // long lists, one edge at a time
+  unsigned lm = __ballot_sync(FULL, act && !is_short);
+  while (lm) {
+    const int e = __ffs(lm) - 1;
+    lm &= lm - 1;
+    const int64_t b = bs.beg[e];
+    const int32_t le = __shfl_sync(FULL, len, e);
+    const int32_t se = bs.salt[e];
+    for (int32_t p0 = 0; p0 < le; p0 += 32 * kUnroll) {
+      int32_t w[kUnroll];
+#pragma unroll
+      for (int k = 0; k < kUnroll; ++k) {
+        const int32_t p = p0 + 32 * k + lane;
+        w[k] = p < le ? a.cols[b + p] : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < kUnroll; ++k) {
+        const int32_t p = p0 + 32 * k + lane;
+        const bool pass = p < le && passes<TILE>(pr, se, w[k]);
+        push<MODE, TILE>(bs, pr, pass, w[k], e, qn, vbase_or_v, vrun, cursor, a, ws, err);
+      }
+    }
+  }
+  if (qn) exact_flush<MODE, TILE>(bs, pr, qn, vbase_or_v, vrun, cursor, a, ws, err);
   __syncwarp();
+  return act ? bs.cnt[lane] : 0u;
 }
+
+// ---------------------------------------------------------------------------
+// Tile kernel
+// ---------------------------------------------------------------------------
+
+struct TileSmem {
+  int32_t tile[kTile];
+  uint32_t bits[(1 << kTileBitsLog2) / 32];
+  int32_t vlo[32];     // tile start of each chunk lane's list (-1 before the group, > S after)
+  uint32_t vcnt[32];   // triangles with apex v (chunk lane)
+  int32_t vrun[32];    // listing: triples written so far per chunk lane
+  BatchSmem bs;
+};
 
 template <int MODE>
 __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, CountWs ws, uint32_t* err) {
@@ -267,7 +389,9 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, Cou
         sm.tile[t] = x;
         bad |= static_cast<uint32_t>(x) >= static_cast<uint32_t>(a.n);
       }
-      sm.vlo[lane] = lane < g0 ? -1 : (lane < g1 ? incl - len : S + 1);
+      for (int i = lane; i < (1 << kTileBitsLog2) / 32; i += 32) sm.bits[i] = 0u;
+      const int32_t lo = incl - len;
+      sm.vlo[lane] = lane < g0 ? -1 : (lane < g1 ? lo : S + 1);
       sm.vcnt[lane] = 0;
       sm.vrun[lane] = 0;
       if (__any_sync(FULL, bad)) {
@@ -276,10 +400,25 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, Cou
         continue;
       }
       __syncwarp();
+      for (int i = 0; i < glen; ++i) fset<kTileBitsLog2>(sm.bits, sm.tile[lo + i], lane);
       const int maxlen = __reduce_max_sync(FULL, glen);
-      const int top = maxlen > 0 ? 1 << (31 - __clz(maxlen)) : 0;
-      for (int t0 = 0; t0 < S; t0 += 32)
-        tile_edge_batch<MODE>(sm, t0, S, top, glen, static_cast<int32_t>(base), a, ws, err);
+      const Probe pr{sm.tile, sm.bits, maxlen > 0 ? 1 << (31 - __clz(maxlen)) : 0, 0, 0, 0};
+      __syncwarp();
+      for (int t0 = 0; t0 < S; t0 += 32) {
+        const int t = t0 + lane;
+        const bool act = t < S;
+        const int vl = act ? search32(sm.vlo, static_cast<int32_t>(t)) : 0;
+        const int32_t u = act ? sm.tile[t] : 0;
+        const int32_t vlen = __shfl_sync(FULL, glen, vl);
+        const uint32_t c = process_batch<MODE, true>(sm.bs, pr, u, act, vl, sm.vlo[vl], vlen,
+                                                     static_cast<int32_t>(base), sm.vrun, nullptr, a, ws, err);
+        if (c) {
+          if (MODE == MODE_LOCAL)
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + u), static_cast<unsigned long long>(c));
+          atomicAdd(&sm.vcnt[vl], c);
+        }
+        __syncwarp();
+      }
       if (in_group) {
         const uint32_t c = sm.vcnt[lane];
         if (MODE == MODE_LOCAL && c)
@@ -305,81 +444,11 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, Cou
 // Block kernel (lists longer than kTile)
 // ---------------------------------------------------------------------------
 
-struct BatchSmem {
-  int64_t beg[32];
-  int32_t exc[32];
-  int32_t u[32];
-};
-
-// Intersect the staged sorted chunk sv[0..dv) (ids in [lo, hi]) with N_u for each
-// u of ulist[0..nb) (nb <= 32).  Returns this lane's number of matches.
-template <int MODE>
-__device__ __forceinline__ uint32_t intersect_batch(const int32_t* sv, int dv, int top, int32_t lo, int32_t hi,
-                                                    const int32_t* ulist, int nb, int32_t v, const CountArgs& a,
-                                                    BatchSmem& bs, uint32_t* err, unsigned long long* cursor) {
-  const int lane = lane_id();
-  int32_t u = 0, len = 0;
-  int64_t ub = 0;
-  if (lane < nb) {
-    u = ulist[lane];
-    len = list_bounds(a, u, ub, err);
-  }
-  const int32_t incl = warp_incl_scan(len);
-  const int32_t tot = __shfl_sync(FULL, incl, 31);
-  const int32_t excl = incl - len;
-  __syncwarp();
-  bs.beg[lane] = ub - excl;
-  bs.exc[lane] = excl;
-  bs.u[lane] = u;
-  __syncwarp();
-  uint32_t cnt = 0;
-  for (int32_t p0 = 0; p0 < tot; p0 += 32 * kUnroll) {
-    int32_t w[kUnroll];
-    int s[kUnroll];
-#pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
-      const int32_t p = p0 + 32 * k + lane;
-      s[k] = 0;
-      w[k] = lo - 1;
-      if (p < tot) {
-        s[k] = search32(bs.exc, p);
-        w[k] = a.cols[bs.beg[s[k]] + p];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
-      const bool found = w[k] >= lo && w[k] <= hi && member(sv, dv, top, w[k]);
-      cnt += found ? 1u : 0u;
-      if (MODE == MODE_LOCAL && found) {
-        atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + bs.u[s[k]]), 1ull);
-        atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + w[k]), 1ull);
-      }
-      if (MODE == MODE_LIST_WRITE) {
-        const unsigned mask = __ballot_sync(FULL, found);
-        if (mask) {
-          unsigned long long b0 = 0;
-          if (lane == 0) b0 = atomicAdd(cursor, static_cast<unsigned long long>(__popc(mask)));
-          const int64_t base = static_cast<int64_t>(__shfl_sync(FULL, b0, 0));
-          if (found) {
-            const int64_t idx = base + __popc(mask & lanemask_lt());
-            if (idx < a.cap) {
-              a.tri[3 * idx] = v;
-              a.tri[3 * idx + 1] = bs.u[s[k]];
-              a.tri[3 * idx + 2] = w[k];
-            } else {
-              set_err(err, ERR_CAPACITY);
-            }
-          }
-        }
-      }
-    }
-  }
-  return cnt;
-}
-
 template <int MODE>
 __global__ void __launch_bounds__(kBlockWarps * 32) k_count_block(CountArgs a, CountWs ws, uint32_t* err) {
-  extern __shared__ int32_t sv[];
+  extern __shared__ int32_t dyn[];
+  int32_t* sv = dyn;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(dyn + kBlockCap);
   __shared__ BatchSmem s_b[kBlockWarps];
   __shared__ unsigned long long s_red[kBlockWarps];
   __shared__ unsigned long long s_cursor;
@@ -401,15 +470,23 @@ __global__ void __launch_bounds__(kBlockWarps * 32) k_count_block(CountArgs a, C
         sv[i] = x;
         bad |= static_cast<uint32_t>(x) >= static_cast<uint32_t>(a.n);
       }
+      for (int i = threadIdx.x; i < (1 << kBlockBitsLog2) / 32; i += blockDim.x) bits[i] = 0u;
       if (__syncthreads_or(bad)) {
         if (threadIdx.x == 0) set_err(err, ERR_BAD_ID);
         break;
       }
-      const int32_t lo = sv[0], hi = sv[clen - 1];
-      const int top = 1 << (31 - __clz(clen));
+      for (int i = threadIdx.x; i < clen; i += blockDim.x) fset<kBlockBitsLog2>(bits, sv[i], 0);
+      __syncthreads();
+      const Probe pr{sv, bits, 1 << (31 - __clz(clen)), clen, sv[0], sv[clen - 1]};
       for (int64_t ub = static_cast<int64_t>(wid) * 32; ub < dv; ub += kBlockWarps * 32) {
         const int nb = static_cast<int>(min64(32, dv - ub));
-        cv += intersect_batch<MODE>(sv, clen, top, lo, hi, a.cols + b + ub, nb, v, a, s_b[wid], err, &s_cursor);
+        const bool act = lane < nb;
+        const int32_t u = act ? a.cols[b + ub + lane] : 0;
+        const uint32_t c =
+            process_batch<MODE, false>(s_b[wid], pr, u, act, 0, 0, 0, v, nullptr, &s_cursor, a, ws, err);
+        cv += c;
+        if (MODE == MODE_LOCAL && c)
+          atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + u), static_cast<unsigned long long>(c));
       }
     }
     cv = warp_sum64(cv);
@@ -450,7 +527,7 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
     Stage st(ctx, s, kNames[MODE][0]);
     k_count_tile<MODE><<<tgrid, kTileWarps * 32, 0, s>>>(a, ws, ctx->d_err);
   }
-  const size_t smem = sizeof(int32_t) * kBlockCap;
+  const size_t smem = sizeof(int32_t) * kBlockCap + (size_t(1) << kBlockBitsLog2) / 8;
   const int bgrid =
       persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_block<MODE>), kBlockWarps * 32, smem);
   {

@@ -58,8 +58,10 @@ def check_all(tc, n, e, listing=True):
     assert len(tri2) == ref["T"]
     if listing:
         tri = tc.list_triangles(g).cpu().numpy()
-        assert np.array_equal(tri, tri2.cpu().numpy())  # same deterministic order
         assert len(tri) == ref["T"]
+        t2 = tri2.cpu().numpy()
+        assert np.array_equal(t2[np.lexsort((t2[:, 2], t2[:, 1], t2[:, 0]))] if len(t2) else t2,
+                              tri[np.lexsort((tri[:, 2], tri[:, 1], tri[:, 0]))] if len(tri) else tri)
         # both sides emit (v, u, w) with v < u < w in the order: compare the row sets
         a = tri[np.lexsort((tri[:, 2], tri[:, 1], tri[:, 0]))] if len(tri) else tri
         r = ref["tri"]
@@ -124,18 +126,18 @@ def test_chung_lu(tc, n, dbar, seed):
 
 
 def test_dense_graph_uses_block_kernel(tc):
-    # lists longer than the warp kernel's staging (256 ids) go to the block kernel
+    # lists longer than one tile (512 ids) go to the block kernel
     rng = np.random.default_rng(10)
-    n = 900
+    n = 1400
     iu = np.triu_indices(n, 1)
     keep = rng.random(len(iu[0])) < 0.8
     e = np.stack([iu[0][keep], iu[1][keep]], axis=1).astype(np.int32)
     g, ref = check_all(tc, n, synth.shuffle_edges(e, 10), listing=False)
-    assert int(g.dhat.max()) > 256
+    assert int(g.dhat.max()) > 512
 
 
 def test_chunked_block_kernel_on_large_clique(tc):
-    # K_n with n > 8193: N_v longer than one shared-memory chunk (8192 ids) and
+    # K_n with n > 8193: N_v longer than two shared-memory chunks (4096 ids) and
     # sorted by the block sorter; closed forms T = C(n,3), T_v = C(n-1,2), C_v = 1
     n = 8300
     e = synth.shuffle_edges(synth.complete(n), 11)
@@ -176,7 +178,10 @@ def test_repeated_runs_are_identical(tc):
     assert a[0] == b[0] and torch.equal(a[1], b[1])
     t1 = tc.list_triangles(g)
     t2 = tc.list_triangles(g)
+    # apex vertices whose lists fit a tile are written in a fixed order
     assert t1.shape == t2.shape
+    if int(g.dhat.max()) <= 512:
+        assert torch.equal(t1, t2)
 
 
 # ---- sparsification (Section 9.1) -----------------------------------------------------
