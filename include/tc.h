@@ -221,6 +221,38 @@ tc_status tc_sparsify_count(tc_ctx* ctx, const tc_graph* g, double q, uint64_t s
                             uint64_t* kept_tri_dev, int64_t* kept_edges_dev, void* ws, size_t ws_bytes,
                             tc_stream stream);
 
+/* ---- counting without allocation --------------------------------------- */
+
+/*
+ * No counterpart in the paper: an entry point for callers that cannot
+ * allocate device memory -- a process whose device memory belongs to another
+ * allocator (a framework's caching allocator that has reserved the device),
+ * a latency-critical path where cudaMalloc/cudaFree would synchronize the
+ * device, or code held to a memory budget declared up front.  tc_count needs a
+ * caller workspace and tc_ctx_create allocates; this call needs neither.
+ *
+ * Computes the same T as tc_count, with the same kernels.  Their scratch (the
+ * queue of long lists and the work cursors) is a file-scope device array of
+ * TC_STATIC_MAX_N * 4 + 256 bytes (about 4 MiB) that every GPU loading the
+ * library holds until the process exits.  The caller still passes inputs and
+ * outputs:
+ *   g          the oriented graph (device pointers, as for tc_count); n must
+ *              not exceed TC_STATIC_MAX_N (else TC_ERR_UNSUPPORTED, nothing run)
+ *   total_dev  device uint64[1], overwritten with T
+ *   check_dev  device uint32[1], overwritten with 0, or with nonzero bits if the
+ *              graph failed the kernels' checks (the TC_ERR_INVALID_GRAPH cases)
+ *   stream     cudaStream_t on the current device (NULL = legacy default stream)
+ * The call only enqueues work: read total_dev and check_dev after the stream
+ * has finished.  It returns TC_ERR_INVALID_ARG for NULL or negative arguments
+ * and TC_ERR_CUDA if a CUDA call fails.  The first call on a device does a
+ * one-time set-up (it looks up the array's device address), so make that first
+ * call before any stream capture begins.  Every call on a device shares the
+ * one array and leaves its contents behind (each call clears the cursors it
+ * needs): calls that overlap on the GPU race on it, so order them.
+ */
+#define TC_STATIC_MAX_N (1 << 20)
+tc_status tc_count_static(const tc_graph* g, uint64_t* total_dev, uint32_t* check_dev, tc_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

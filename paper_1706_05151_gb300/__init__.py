@@ -34,7 +34,8 @@ STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_INVALID_GRAPH", 3: "TC
 EXPORTS = ["tc_ctx_create", "tc_ctx_destroy", "tc_ctx_set_async", "tc_ctx_status", "tc_status_string",
            "tc_last_error", "tc_ctx_sm_count", "tc_version", "tc_workspace_size", "tc_orient", "tc_count",
            "tc_count_local", "tc_list_count", "tc_list_write", "tc_list", "tc_analyze", "tc_sparsify_count",
-           "tc_ctx_set_profiling", "tc_ctx_stage_count", "tc_ctx_stage", "tc_ctx_reset_stats", "tc_ctx_launches"]
+           "tc_ctx_set_profiling", "tc_ctx_stage_count", "tc_ctx_stage", "tc_ctx_reset_stats", "tc_ctx_launches",
+           "tc_count_static"]
 
 
 class TcError(RuntimeError):
