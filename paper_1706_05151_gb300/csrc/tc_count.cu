@@ -357,7 +357,9 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, Cou
       }
     }
     const int64_t d = e - b;
-    const bool big = valid && d > kTile;
+    // the listing write pass only revisits apex vertices that have triangles
+    const bool skip = MODE == MODE_LIST_WRITE && valid && ws.vcount[v] == 0;
+    const bool big = valid && !skip && d > kTile;
     const unsigned bigmask = __ballot_sync(FULL, big);
     if (bigmask) {
       uint32_t qb = 0;
@@ -368,12 +370,12 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, Cou
     // Groups: maximal runs of consecutive short lists whose ids fit one tile.
     int g0 = 0;
     while (g0 < 32) {
-      const int32_t len = (lane >= g0 && valid && !big) ? static_cast<int32_t>(d) : 0;
+      const int32_t len = (lane >= g0 && valid && !big && !skip) ? static_cast<int32_t>(d) : 0;
       const int32_t incl = warp_incl_scan(len);
-      const bool stop = lane >= g0 && (!valid || big || incl > kTile);
+      const bool stop = lane >= g0 && (!valid || big || skip || incl > kTile);
       const unsigned smask = __ballot_sync(FULL, stop);
       const int g1 = smask ? __ffs(smask) - 1 : 32;
-      if (g1 == g0) {  // lane g0 is past the end or a queued long list
+      if (g1 == g0) {  // lane g0 is past the end, a queued long list or skipped
         if (!__shfl_sync(FULL, valid, g0)) break;
         ++g0;
         continue;
