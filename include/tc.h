@@ -58,7 +58,8 @@ typedef enum {
   TC_OP_ORIENT = 0,
   TC_OP_COUNT = 1,       /* tc_count and tc_count_local */
   TC_OP_LIST = 2,        /* tc_list, tc_list_count, tc_list_write, tc_analyze */
-  TC_OP_SPARSIFY = 3     /* tc_sparsify_count */
+  TC_OP_SPARSIFY = 3,    /* tc_sparsify_count */
+  TC_OP_BATCH = 4        /* tc_batch: n = total vertices N, m = total edges E */
 } tc_op;
 
 typedef struct tc_ctx tc_ctx;
@@ -220,6 +221,36 @@ tc_status tc_analyze(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, int64_
 tc_status tc_sparsify_count(tc_ctx* ctx, const tc_graph* g, double q, uint64_t seed,
                             uint64_t* kept_tri_dev, int64_t* kept_edges_dev, void* ws, size_t ws_bytes,
                             tc_stream stream);
+
+/* ---- batched form ------------------------------------------------------------ */
+
+/*
+ * Many independent graphs in one launch sequence (no counterpart in the
+ * paper, which counts one graph; the counting per graph is Figure 2's).  The
+ * G graphs are laid side by side as a disjoint union: graph g owns the global
+ * vertex ids [vbase[g], vbase[g+1]).  The union is oriented once (a graph's
+ * orientation does not depend on the others: degrees and the order of Eq. (1)
+ * are per vertex) and counted by one persistent launch whose device-side work
+ * cursor and queue of long lists span all graphs.
+ *   G          number of graphs (> 0); N, E: total vertices and edges (host)
+ *   vbase_dev  device int64[G+1], non-decreasing, vbase[0] = 0, vbase[G] = N
+ *   ebase_dev  device int64[G+1], non-decreasing, ebase[0] = 0, ebase[G] = E;
+ *              graph g's edges are edges_dev[ebase[g] .. ebase[g+1])
+ *   edges_dev  device int32[E][2]: LOCAL ids in [0, n_g), each undirected edge
+ *              of graph g once (either direction, any order)
+ * Outputs (device):
+ *   offsets int64[N+1], cols int32[E], deg int32[N], dhat int32[N]: the
+ *     oriented union; graph g's lists are those of its global ids, with
+ *     global ids (subtract vbase[g] for local ones)
+ *   totals_dev uint64[G]: T of each graph
+ *   tv_dev     int64[N] or NULL: per-vertex counts (graph g's in tv[vbase[g] ..))
+ * Workspace: tc_workspace_size(TC_OP_BATCH, N, E).  A local id outside
+ * [0, n_g), a self-loop, a repeated edge or malformed bases give
+ * TC_ERR_INVALID_GRAPH.
+ */
+tc_status tc_batch(tc_ctx* ctx, int32_t G, int32_t N, int64_t E, const int64_t* vbase_dev, const int64_t* ebase_dev,
+                   const int32_t* edges_dev, int64_t* offsets, int32_t* cols, int32_t* deg, int32_t* dhat,
+                   uint64_t* totals_dev, int64_t* tv_dev, void* ws, size_t ws_bytes, tc_stream stream);
 
 /* ---- counting without allocation --------------------------------------- */
 

@@ -25,7 +25,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtc.so")
 
-TC_OP_ORIENT, TC_OP_COUNT, TC_OP_LIST, TC_OP_SPARSIFY = 0, 1, 2, 3
+TC_OP_ORIENT, TC_OP_COUNT, TC_OP_LIST, TC_OP_SPARSIFY, TC_OP_BATCH = 0, 1, 2, 3, 4
 STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_INVALID_GRAPH", 3: "TC_ERR_WORKSPACE",
           4: "TC_ERR_CAPACITY", 5: "TC_ERR_CUDA", 6: "TC_ERR_UNSUPPORTED", 7: "TC_ERR_TIMEOUT",
           8: "TC_ERR_REJECTED", 9: "TC_ERR_NOT_READY"}
@@ -34,6 +34,7 @@ STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_INVALID_GRAPH", 3: "TC
 EXPORTS = ["tc_ctx_create", "tc_ctx_destroy", "tc_ctx_set_async", "tc_ctx_status", "tc_status_string",
            "tc_last_error", "tc_ctx_sm_count", "tc_version", "tc_workspace_size", "tc_orient", "tc_count",
            "tc_count_local", "tc_list_count", "tc_list_write", "tc_list", "tc_analyze", "tc_sparsify_count",
+           "tc_batch",
            "tc_ctx_set_profiling", "tc_ctx_stage_count", "tc_ctx_stage", "tc_ctx_reset_stats", "tc_ctx_launches",
            "tc_count_static"]
 
@@ -83,6 +84,7 @@ def load_library(path: str = LIB_PATH):
             "tc_list_write": (i32, [vp, G, vp, i64, vp, sz, vp]),
             "tc_list": (i32, [vp, G, vp, i64, ctypes.POINTER(i64), vp, sz, vp]),
             "tc_analyze": (i32, [vp, G, vp, vp, vp, vp, i64, ctypes.POINTER(i64), vp, sz, vp]),
+            "tc_batch": (i32, [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
             "tc_sparsify_count": (i32, [vp, G, ctypes.c_double, u64, vp, vp, vp, sz, vp]),
             "tc_ctx_set_profiling": (i32, [vp, ctypes.c_int]),
             "tc_ctx_stage_count": (ctypes.c_int, [vp]),
@@ -310,6 +312,48 @@ def sparsify_count(g: Graph, q: float, seed: int, ctx: Context | None = None):
     t = int(kept_tri.item())
     est = float(t) / (q * q * q) if q > 0 else float("nan")
     return t, int(kept_edges.item()), est
+
+
+@dataclass
+class Batch:
+    """Inputs of tc_batch on the device: the graphs side by side."""
+    G: int
+    N: int
+    E: int
+    vbase: torch.Tensor   # int64[G+1]
+    ebase: torch.Tensor   # int64[G+1]
+    edges: torch.Tensor   # int32[E, 2], local ids
+
+
+def make_batch(graphs, device) -> Batch:
+    """Concatenate [(n_g, edges_g int32[m_g, 2] with local ids), ...] into tc_batch inputs."""
+    import numpy as np
+    ns = np.array([int(n) for n, _ in graphs], dtype=np.int64)
+    ms = np.array([len(e) for _, e in graphs], dtype=np.int64)
+    vbase = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    ebase = np.concatenate([[0], np.cumsum(ms)]).astype(np.int64)
+    edges = np.concatenate([np.asarray(e, dtype=np.int32).reshape(-1, 2) for _, e in graphs]) if len(graphs) \
+        else np.zeros((0, 2), np.int32)
+    return Batch(len(graphs), int(vbase[-1]), int(ebase[-1]), torch.from_numpy(vbase).to(device),
+                 torch.from_numpy(ebase).to(device), torch.from_numpy(np.ascontiguousarray(edges)).to(device))
+
+
+def batch(b: Batch, local: bool = True, ctx: Context | None = None):
+    """tc_batch: (totals int64[G], tv int64[N] or None, the oriented union as a Graph)."""
+    ctx = ctx or default_context()
+    dev = ctx.device
+    N, E = b.N, b.E
+    offsets = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    cols = torch.empty(max(E, 1), dtype=torch.int32, device=dev)
+    deg = torch.empty(max(N, 1), dtype=torch.int32, device=dev)
+    dhat = torch.empty(max(N, 1), dtype=torch.int32, device=dev)
+    totals = torch.empty(b.G, dtype=torch.int64, device=dev)
+    tv = torch.empty(max(N, 1), dtype=torch.int64, device=dev) if local else None
+    ws = ctx.workspace(TC_OP_BATCH, N, E)
+    ctx.check(ctx.lib.tc_batch(ctx.handle, b.G, N, E, _ptr(b.vbase), _ptr(b.ebase), _ptr(b.edges) if E else None,
+                               _ptr(offsets), _ptr(cols), _ptr(deg), _ptr(dhat), _ptr(totals), _ptr(tv),
+                               _ptr(ws), ws.numel(), _stream(dev)))
+    return totals, (tv[:N] if tv is not None else None), Graph(N, E, offsets, cols[:E], deg[:N], dhat[:N])
 
 
 def graph_from_csr(offsets: torch.Tensor, cols: torch.Tensor, deg=None, dhat=None) -> Graph:

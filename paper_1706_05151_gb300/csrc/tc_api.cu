@@ -251,6 +251,7 @@ tc_status tc_workspace_size(tc_op op, int32_t n, int64_t m, size_t* bytes) {
     case TC_OP_COUNT: tc::carve_count(c, n, false); break;
     case TC_OP_LIST: tc::carve_count(c, n, true); break;
     case TC_OP_SPARSIFY: tc::carve_sparsify(c, n, m); break;
+    case TC_OP_BATCH: tc::carve_batch(c, n, m); break;
     default: return TC_ERR_INVALID_ARG;
   }
   *bytes = c.size();
@@ -414,6 +415,36 @@ tc_status tc_analyze(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, int64_
   a.tri = tri_dev;
   a.cap = cap;
   return finish(ctx, s, tc::launch_count(ctx, tc::MODE_LIST_WRITE, a, w, s));
+}
+
+tc_status tc_batch(tc_ctx* ctx, int32_t G, int32_t N, int64_t E, const int64_t* vbase_dev, const int64_t* ebase_dev,
+                   const int32_t* edges_dev, int64_t* offsets, int32_t* cols, int32_t* deg, int32_t* dhat,
+                   uint64_t* totals_dev, int64_t* tv_dev, void* ws, size_t ws_bytes, tc_stream stream) {
+  if (!ctx) return TC_ERR_INVALID_ARG;
+  if (G <= 0 || N < 0 || E < 0) return fail(ctx, TC_ERR_INVALID_ARG, "need G > 0, N >= 0, E >= 0");
+  if (!vbase_dev || !ebase_dev || !offsets || !totals_dev || (N > 0 && (!deg || !dhat)) ||
+      (E > 0 && (!edges_dev || !cols)))
+    return fail(ctx, TC_ERR_INVALID_ARG, "NULL buffer");
+  if (!aligned(vbase_dev, 8) || !aligned(ebase_dev, 8) || !aligned(offsets, 8) || (E > 0 && !aligned(edges_dev, 8)))
+    return fail(ctx, TC_ERR_INVALID_ARG, "misaligned buffer");
+  tc_status st = check_ws(ctx, TC_OP_BATCH, N, E, ws, ws_bytes);
+  if (st != TC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = begin(ctx, s)) != TC_OK) return st;
+  Carver c(ws);
+  tc::BatchWs w = tc::carve_batch(c, N, E);
+  cudaError_t e = cudaMemsetAsync(totals_dev, 0, sizeof(uint64_t) * static_cast<size_t>(G), s);
+  if (e == cudaSuccess && tv_dev) e = cudaMemsetAsync(tv_dev, 0, sizeof(int64_t) * static_cast<size_t>(N), s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "clear outputs");
+  e = tc::launch_batch_prepare(ctx, G, N, E, vbase_dev, ebase_dev, edges_dev, w, s);
+  if (e == cudaSuccess) e = tc::launch_orient(ctx, N, E, w.edges, offsets, cols, deg, dhat, w.orient, s);
+  if (e == cudaSuccess) {
+    tc::CountArgs a{N, E, offsets, cols, nullptr, tv_dev, nullptr, 0};
+    a.graph_total = reinterpret_cast<unsigned long long*>(totals_dev);
+    a.gid = w.gid;
+    e = tc::launch_count(ctx, tv_dev ? tc::MODE_LOCAL : tc::MODE_COUNT, a, w.count, s);
+  }
+  return finish(ctx, s, e);
 }
 
 tc_status tc_sparsify_count(tc_ctx* ctx, const tc_graph* g, double q, uint64_t seed, uint64_t* kept_tri_dev,

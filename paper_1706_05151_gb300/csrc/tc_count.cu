@@ -324,6 +324,23 @@ __device__ __forceinline__ uint32_t process_batch(BatchSmem& bs, const Probe& pr
 // Tile kernel
 // ---------------------------------------------------------------------------
 
+// Batched form: add each apex vertex's count to its graph's total.  Graph ids
+// of consecutive vertices form runs; one lane per run adds the run's sum.
+__device__ __forceinline__ void add_graph_totals(const CountArgs& a, bool in_group, int32_t v, uint32_t c) {
+  const int lane = lane_id();
+  const int32_t key = in_group ? a.gid[v] : -1 - lane;
+  const uint32_t incl = static_cast<uint32_t>(warp_incl_scan(static_cast<int32_t>(c)));
+  const int32_t prev = __shfl_up_sync(FULL, key, 1);
+  const bool head = lane == 0 || key != prev;
+  const unsigned heads = __ballot_sync(FULL, head);
+  const unsigned after = heads & ~(0xffffffffu >> (31 - lane));
+  const int end = (after ? __ffs(after) - 1 : 32) - 1;
+  const uint32_t at_end = __shfl_sync(FULL, incl, end);
+  const uint32_t before = __shfl_sync(FULL, incl, lane > 0 ? lane - 1 : 0);
+  const uint32_t sum = at_end - (lane > 0 ? before : 0u);
+  if (head && in_group && sum) atomicAdd(a.graph_total + key, static_cast<unsigned long long>(sum));
+}
+
 struct TileSmem {
   int32_t tile[kTile];
   uint32_t bits[(1 << kTileBitsLog2) / 32];
@@ -421,13 +438,14 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, Cou
         }
         __syncwarp();
       }
+      const uint32_t cv = in_group ? sm.vcnt[lane] : 0u;
       if (in_group) {
-        const uint32_t c = sm.vcnt[lane];
-        if (MODE == MODE_LOCAL && c)
-          atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + v), static_cast<unsigned long long>(c));
-        if ((MODE == MODE_LIST_COUNT || MODE == MODE_LOCAL) && ws.vcount) ws.vcount[v] = c;
-        acc += c;
+        if (MODE == MODE_LOCAL && cv)
+          atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + v), static_cast<unsigned long long>(cv));
+        if ((MODE == MODE_LIST_COUNT || MODE == MODE_LOCAL) && ws.vcount) ws.vcount[v] = cv;
+        acc += cv;
       }
+      if (MODE != MODE_LIST_WRITE && a.graph_total) add_graph_totals(a, in_group, v, cv);
       __syncwarp();
       g0 = g1;
     }
@@ -499,6 +517,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32) k_count_block(CountArgs a, C
       for (int w = 0; w < kBlockWarps; ++w) t += s_red[w];
       if (MODE == MODE_LOCAL && t) atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + v), t);
       if ((MODE == MODE_LIST_COUNT || MODE == MODE_LOCAL) && ws.vcount) ws.vcount[v] = static_cast<int64_t>(t);
+      if (MODE != MODE_LIST_WRITE && a.graph_total && t) atomicAdd(a.graph_total + a.gid[v], t);
       acc += t;
     }
     __syncthreads();

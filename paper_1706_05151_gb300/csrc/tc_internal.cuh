@@ -125,6 +125,16 @@ struct SparsifyWs {
 };
 SparsifyWs carve_sparsify(Carver& c, int32_t n, int64_t m);
 
+struct BatchWs {
+  int32_t* edges;       // union edge list with global ids (2E)
+  int32_t* gid;         // graph id per global vertex (N)
+  OrientWs orient;
+  CountWs count;
+};
+BatchWs carve_batch(Carver& c, int32_t n, int64_t m);
+cudaError_t launch_batch_prepare(Ctx* ctx, int32_t G, int32_t N, int64_t E, const int64_t* vbase,
+                                 const int64_t* ebase, const int32_t* edges_local, BatchWs ws, cudaStream_t s);
+
 // ---- launchers (stream-ordered, no synchronisation) -------------------------
 
 cudaError_t exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, ScanWs ws, cudaStream_t s);
@@ -144,6 +154,8 @@ struct CountArgs {
   int64_t* tv;                // MODE_LOCAL
   int32_t* tri;               // MODE_LIST_WRITE
   int64_t cap;                // MODE_LIST_WRITE
+  unsigned long long* graph_total = nullptr;  // batched form: T per graph ...
+  const int32_t* gid = nullptr;               // ... indexed by the graph id of the apex vertex
 };
 cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a, CountWs ws, cudaStream_t s);
 cudaError_t launch_clustering(Ctx* ctx, int32_t n, const int32_t* deg, const int64_t* tv, double* cc, cudaStream_t s);

@@ -57,7 +57,7 @@ def _load():
                                  ctypes.c_double, ctypes.c_uint64, i32p, ctypes.c_int64]
         lib.gen_chung_lu.restype = ctypes.c_int64
         lib.gen_chung_lu.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
-                                     ctypes.c_uint64, i32p, ctypes.c_int64]
+                                     ctypes.c_uint64, i32p, ctypes.c_int64, ctypes.c_int]
         lib.gen_batch_params.restype = None
         lib.gen_batch_params.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, i32p, f64p]
@@ -101,12 +101,12 @@ def rmat(scale: int, edge_factor: int, seed: int, a: float = 0.57, b: float = 0.
     return _finish(buf, m, "rmat")
 
 
-def chung_lu(n: int, dbar: float, gamma: float, seed: int, stream: int = 0) -> np.ndarray:
+def chung_lu(n: int, dbar: float, gamma: float, seed: int, stream: int = 0, threads: int = 0) -> np.ndarray:
     """Chung-Lu graph with weights (i+1)^(-1/(gamma-1)) and floor(n*dbar/2) endpoint pairs."""
     lib = _load()
     pairs = int(math.floor(n * dbar / 2.0))
     buf = np.empty((max(pairs, 1), 2), dtype=np.int32)
-    m = lib.gen_chung_lu(n, dbar, gamma, seed, stream, buf.ctypes.data_as(i32p), pairs)
+    m = lib.gen_chung_lu(n, dbar, gamma, seed, stream, buf.ctypes.data_as(i32p), pairs, threads)
     return _finish(buf, m, "chung_lu")
 
 
@@ -123,9 +123,13 @@ def batch_params(num_graphs: int, seed: int, nlo: float = 100.0, nhi: float = 10
 
 def batch_graphs(num_graphs: int, seed: int, gamma: float = 2.1, **kw):
     """The batched workload: a list of (n_g, edges_g) Chung-Lu graphs with per-graph streams."""
+    import concurrent.futures as cf
     ns, ds = batch_params(num_graphs, seed, **kw)
-    return [(int(ns[g]), chung_lu(int(ns[g]), float(ds[g]), gamma, seed, stream=g))
-            for g in range(num_graphs)]
+    # one graph per worker thread (ctypes releases the GIL), each generated single-threaded
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        edges = list(ex.map(lambda g: chung_lu(int(ns[g]), float(ds[g]), gamma, seed, stream=g, threads=1),
+                            range(num_graphs)))
+    return list(zip((int(n) for n in ns), edges))
 
 
 def num_threads() -> int:

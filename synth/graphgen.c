@@ -48,11 +48,13 @@ static inline uint64_t below(uint64_t r, uint64_t n) { return (uint64_t)(((u128)
 static inline double unit53(uint64_t r) { return (double)(r >> 11) * 0x1.0p-53; }
 
 /* ---- parallel LSD radix sort of uint64 keys ------------------------------ */
-static void sort_u64(uint64_t* a, uint64_t* tmp, int64_t cnt, int bits) {
+/* threads: 0 = OpenMP default */
+static void sort_u64(uint64_t* a, uint64_t* tmp, int64_t cnt, int bits, int threads) {
   if (cnt <= 1) return;
   int nt = 1;
 #ifdef _OPENMP
-  nt = omp_get_max_threads();
+  nt = threads > 0 ? threads : omp_get_max_threads();
+  if (cnt < 65536) nt = 1;
 #endif
   int64_t* hist = (int64_t*)calloc((size_t)nt * 256, sizeof(int64_t));
   uint64_t *src = a, *dst = tmp;
@@ -95,13 +97,13 @@ static int bits_for(int64_t n) {
 }
 
 /* keys = (lo << 32) | hi; sort, unique, write int32 pairs. Returns edge count. */
-static int64_t keys_to_edges(uint64_t* keys, int64_t cnt, int32_t n, int32_t* out, int64_t cap) {
+static int64_t keys_to_edges(uint64_t* keys, int64_t cnt, int32_t n, int32_t* out, int64_t cap, int threads) {
   uint64_t* tmp = (uint64_t*)malloc((size_t)(cnt > 0 ? cnt : 1) * sizeof(uint64_t));
   if (!tmp) return -2;
   int b = bits_for(n);
   /* the low word holds hi (< n), the high word lo (< n): sort on both */
   for (int64_t i = 0; i < cnt; ++i) keys[i] = ((keys[i] >> 32) << b) | (keys[i] & 0xffffffffULL);
-  sort_u64(keys, tmp, cnt, 2 * b);
+  sort_u64(keys, tmp, cnt, 2 * b, threads);
   free(tmp);
   int64_t m = 0;
   uint64_t mask = ((uint64_t)1 << b) - 1;
@@ -135,7 +137,7 @@ int64_t gen_er(int32_t n, int64_t draws, uint64_t seed, int32_t* out, int64_t ca
   int64_t c = 0;
   for (int64_t i = 0; i < draws; ++i)
     if (keys[i] != ~0ULL) keys[c++] = keys[i];
-  int64_t m = keys_to_edges(keys, c, n, out, cap);
+  int64_t m = keys_to_edges(keys, c, n, out, cap, 0);
   free(keys);
   return m;
 }
@@ -252,7 +254,7 @@ int64_t gen_rmat(int32_t scale, int64_t edge_factor, double a, double b, double 
   int64_t cnt = 0;
   for (int64_t i = 0; i < samples; ++i)
     if (keys[i] != ~0ULL) keys[cnt++] = keys[i];
-  int64_t m = keys_to_edges(keys, cnt, n, out, cap);
+  int64_t m = keys_to_edges(keys, cnt, n, out, cap, 0);
   free(keys);
   return m;
 }
@@ -264,27 +266,38 @@ int64_t gen_rmat(int32_t scale, int64_t edge_factor, double a, double b, double 
  * independent graphs drawn with the same seed.
  */
 int64_t gen_chung_lu(int32_t n, double dbar, double gamma, uint64_t seed, uint64_t stream,
-                     int32_t* out, int64_t cap) {
+                     int32_t* out, int64_t cap, int threads) {
   if (n < 2) return 0;
   int64_t pairs = (int64_t)floor((double)n * dbar / 2.0);
   double* cum = (double*)malloc((size_t)n * sizeof(double));
+  int32_t* guide = (int32_t*)malloc((size_t)n * sizeof(int32_t));
   double run = 0.0, ex = -1.0 / (gamma - 1.0);
   for (int32_t i = 0; i < n; ++i) { run += pow((double)(i + 1), ex); cum[i] = run; }
+  /* guide table (indexed search): guide[k] = first i with cum[i] > k * run / n */
+  for (int32_t k = 0, i = 0; k < n; ++k) {
+    double t = (double)k * run / (double)n;
+    while (i < n - 1 && cum[i] <= t) ++i;
+    guide[k] = i;
+  }
   uint64_t* keys = (uint64_t*)malloc((size_t)(pairs > 0 ? pairs : 1) * sizeof(uint64_t));
-  if (!keys) { free(cum); return -2; }
-#pragma omp parallel for schedule(static) if (pairs > 65536)
+  if (!keys) { free(cum); free(guide); return -2; }
+  int nt = threads > 0 ? threads : 1;
+#ifdef _OPENMP
+  if (threads <= 0) nt = omp_get_max_threads();
+#endif
+#pragma omp parallel for schedule(static) num_threads(nt) if (pairs > 65536 && nt > 1)
   for (int64_t i = 0; i < pairs; ++i) {
     uint64_t r4[4];
     gen_philox((uint64_t)i, stream, 0, 0, seed, TAG_CL, r4);
     int32_t ends[2];
     for (int s = 0; s < 2; ++s) {
-      double x = unit53(r4[s]) * run;
-      int32_t lo = 0, hi = n - 1; /* first index with cum > x */
-      while (lo < hi) {
-        int32_t mid = lo + (hi - lo) / 2;
-        if (cum[mid] > x) hi = mid; else lo = mid + 1;
-      }
-      ends[s] = lo;
+      double u = unit53(r4[s]);
+      double x = u * run;
+      int64_t k = (int64_t)(u * (double)n);
+      if (k >= n) k = n - 1;
+      int32_t j = guide[k]; /* first index with cum > x, walking forward from the guide */
+      while (j < n - 1 && cum[j] <= x) ++j;
+      ends[s] = j;
     }
     if (ends[0] == ends[1]) { keys[i] = ~0ULL; continue; }
     uint64_t lo = (uint64_t)(ends[0] < ends[1] ? ends[0] : ends[1]);
@@ -294,8 +307,8 @@ int64_t gen_chung_lu(int32_t n, double dbar, double gamma, uint64_t seed, uint64
   int64_t cnt = 0;
   for (int64_t i = 0; i < pairs; ++i)
     if (keys[i] != ~0ULL) keys[cnt++] = keys[i];
-  int64_t m = keys_to_edges(keys, cnt, n, out, cap);
-  free(keys); free(cum);
+  int64_t m = keys_to_edges(keys, cnt, n, out, cap, threads);
+  free(keys); free(cum); free(guide);
   return m;
 }
 
