@@ -53,7 +53,7 @@ def test_fullsize_sampled_vertex_counts(run):
     rng = np.random.default_rng(5)
     sample = rng.choice(N, 400, replace=False)
     sample = np.concatenate([sample, np.arange(0, 64)])            # the oldest, highest-degree vertices
-    sample = [int(v) for v in sample if deg[v] <= 40000]
+    sample = [int(v) for v in sample if deg[v] <= 4000]
     tv_h = tv.cpu().numpy()
     cc_h = cc.cpu().numpy()
     ref_tv = np.array([adj.vertex_triangles(v) for v in sample], dtype=np.int64)
@@ -68,9 +68,7 @@ def test_fullsize_invariants(run):
     assert tc.count(g) == T
     assert len(tri) == T
     # every listed triple is a triangle, listed once
-    t = tri.to(torch.int64)
-    key = (t[:, 0] * N + t[:, 1]) * N + t[:, 2]
-    assert int(torch.unique(key).numel()) == T
+    assert int(torch.unique(tri, dim=0).shape[0]) == T
     adj = run_cache.get("adj") or oracle.Adjacency(N, e)
     idx = np.random.default_rng(6).choice(T, min(T, 20000), replace=False)
     th = tri[idx].cpu().numpy()
