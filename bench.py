@@ -255,6 +255,101 @@ def bench_batched(tc, ctx, dev, args, rank):
             "batched_edges_per_s": E / (batched_ms * 1e-3), "results_equal": same}
 
 
+def serving_pool():
+    """The serving configuration's graph pool (seeded): ER n = 2^12..2^18 with mean
+    degree 16, R-MAT scale 16..20 with edge factor 16, Chung-Lu (gamma 2.1) with
+    n = 1e4..1e6 and mean degree 16."""
+    import synth
+    pool = []
+    for lg in (12, 14, 16, 18):
+        pool.append((f"ER n=2^{lg}", 1 << lg, synth.er(1 << lg, 8 << lg, 100 + lg)))
+    for sc in (16, 18, 20):
+        pool.append((f"R-MAT scale {sc}", 1 << sc, synth.rmat(sc, 16, 200 + sc)))
+    for n in (10 ** 4, 10 ** 5, 10 ** 6):
+        pool.append((f"Chung-Lu n={n}", n, synth.chung_lu(n, 16.0, 2.1, 300, n)))
+    return pool
+
+
+def bench_serving(tc, dev, args):
+    """Poisson arrivals of count / local / list requests (60/30/10) on resident graphs."""
+    import threading
+    import torch
+    free, _ = torch.cuda.mem_get_info(dev)
+    pool_bytes = int(min(args.serve_pool_gb * 1e9, free - 8e9))
+    srv = tc.Server(pool_bytes, slots=8)
+    graphs = serving_pool()
+    gids = [srv.add_graph(n, e) for _, n, e in graphs]
+    m_of = {gid: len(e) for gid, (_, _, e) in zip(gids, graphs)}
+    kinds_p = [0.6, 0.3, 0.1]
+    # capacity: mean service time of the mix, one request at a time
+    service = {}
+    for gid in gids:
+        for kind in range(3):
+            srv.wait(srv.submit(gid, kind), copy=False)
+            t0 = time.perf_counter()
+            for _ in range(3):
+                srv.wait(srv.submit(gid, kind), copy=False)
+            service[(gid, kind)] = (time.perf_counter() - t0) / 3
+    mean_service = sum(kinds_p[k] * service[(g, k)] for g in gids for k in range(3)) / len(gids)
+    capacity = 1.0 / mean_service
+    out = {"workload": "; ".join(name for name, _, _ in graphs), "pool_gb": pool_bytes / 1e9, "slots": 8,
+           "mix": "60% count, 30% local (T_v, C_v), 10% list", "sequential_capacity_rps": capacity, "rates": []}
+    for li, load in enumerate(float(x) for x in args.serve_loads.split(",")):
+        rate = load * capacity
+        warm = 500
+        total = warm + (args.serve_requests if li == 0 else max(args.serve_requests // 2, 1000))
+        rng = np.random.default_rng(1000 + li)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, total))
+        kinds = rng.choice(3, total, p=kinds_p)
+        which = rng.integers(0, len(gids), total)
+        tickets = [None] * total
+        ready = threading.Semaphore(0)
+        t_start = time.perf_counter()
+
+        def submitter():
+            for i in range(total):
+                target = t_start + arrivals[i]
+                while True:
+                    now = time.perf_counter()
+                    if now >= target:
+                        break
+                    if target - now > 0.0004:
+                        time.sleep(target - now - 0.0002)
+                tickets[i] = (srv.submit(gids[which[i]], int(kinds[i])), time.perf_counter())
+                ready.release()
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, lat_kind, edges, statuses = [], {0: [], 1: [], 2: []}, 0, {}
+        t_first = t_last = None
+        for i in range(total):
+            ready.acquire()
+            tk, t_sub = tickets[i]
+            r = srv.wait(tk, timeout_ms=600000, copy=False)
+            statuses[r.status] = statuses.get(r.status, 0) + 1
+            if i >= warm:
+                if t_first is None:
+                    t_first = t_sub
+                lat.append(r.latency_ms)
+                lat_kind[r.kind].append(r.latency_ms)
+                edges += m_of[r.graph_id]
+        th.join()
+        t_last = time.perf_counter()
+        span = t_last - t_first
+        la = np.array(lat)
+        out["rates"].append({
+            "offered_rps": rate, "load": load, "requests": len(lat), "achieved_rps": len(lat) / span,
+            "p50_ms": float(np.percentile(la, 50)), "p99_ms": float(np.percentile(la, 99)),
+            "p50_ms_by_kind": {k: float(np.percentile(v, 50)) for k, v in zip(("count", "local", "list"),
+                                                                                lat_kind.values()) if v},
+            "p99_ms_by_kind": {k: float(np.percentile(v, 99)) for k, v in zip(("count", "local", "list"),
+                                                                                lat_kind.values()) if v},
+            "edges_per_s": edges / span, "statuses": {str(k): v for k, v in statuses.items()}})
+    out["stats"] = srv.stats()
+    srv.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -271,6 +366,10 @@ def main():
     ap.add_argument("--batch-graphs", type=int, default=4096,
                     help="graphs of the batched Chung-Lu workload (0 skips the batched measurement)")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--serve-requests", type=int, default=10000,
+                    help="requests measured per arrival rate (0 skips the serving measurement)")
+    ap.add_argument("--serve-loads", default="0.5,0.85", help="arrival rates as fractions of measured capacity")
+    ap.add_argument("--serve-pool-gb", type=float, default=150.0)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -387,6 +486,11 @@ def main():
     batched = None
     if args.batch_graphs > 0:
         batched = bench_batched(tc, ctx, dev, args, rank)
+    serving = None
+    if args.serve_requests > 0 and world == 1:
+        del g, tv, cc, tri_buf
+        torch.cuda.empty_cache()
+        serving = bench_serving(tc, dev, args)
 
     # ---- roofline of the intersection kernel (per-vertex counting pass) ----
     peak, peak_src = load_peaks()
@@ -430,6 +534,7 @@ def main():
             "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in sorted(stages.items())},
             "cpu_baseline": cpu,
             "batched": batched,
+            "serving": serving,
             "sparsified": {"kept_edges": sp[1], "kept_triangles": sp[0], "estimate": sp[2],
                            "rel_error": abs(sp[2] - T) / T if T else None},
         }

@@ -252,6 +252,83 @@ tc_status tc_batch(tc_ctx* ctx, int32_t G, int32_t N, int64_t E, const int64_t* 
                    const int32_t* edges_dev, int64_t* offsets, int32_t* cols, int32_t* deg, int32_t* dhat,
                    uint64_t* totals_dev, int64_t* tv_dev, void* ws, size_t ws_bytes, tc_stream stream);
 
+/* ---- serving ----------------------------------------------------------------- */
+
+/*
+ * A request server over resident graphs (no counterpart in the paper, whose
+ * per-graph computations it serves: Figure 2's count, Section 11's per-vertex
+ * counts and clustering coefficients, Section 10's listing).  It does
+ * continuous batching: a worker thread admits requests as soon as one of its
+ * slots (a CUDA stream each) and enough pool memory are free, so requests that
+ * arrive while others run join the device at once and overlap with them.
+ *
+ * Memory: the caller gives the server a device pool (pool_dev, pool_bytes,
+ * e.g. 150 GB of HBM); every device byte the server uses -- resident oriented
+ * graphs, per-request workspaces and results -- comes from it.  Admission is
+ * by footprint: a graph that does not fit is refused with TC_ERR_REJECTED; a
+ * request that does not fit yet waits until running requests finish or results
+ * are released, for at most the admission timeout, and one larger than all the
+ * memory the pool could ever free is refused at once.
+ *
+ * Threading: every tc_serve_* call is thread-safe.  Results stay valid (and
+ * their memory held) until tc_serve_release.
+ */
+typedef struct tc_server tc_server;
+
+typedef enum {
+  TC_REQ_COUNT = 0,  /* T */
+  TC_REQ_LOCAL = 1,  /* T, T_v and C_v */
+  TC_REQ_LIST = 2    /* T and the triangle list (v, u, w) */
+} tc_request_kind;
+
+typedef struct {
+  int32_t slots;            /* requests on the GPU at once (0 = 8, at most 64) */
+  int64_t admit_timeout_ms; /* how long a request may wait for memory before TC_ERR_REJECTED (0 = 10 s) */
+} tc_serve_config;
+
+typedef struct {
+  tc_status status;  /* TC_OK, or why the request failed (TC_ERR_REJECTED: did not fit) */
+  int32_t kind;      /* tc_request_kind */
+  int64_t graph_id;
+  int32_t n;         /* vertices of the graph */
+  uint64_t triangles;
+  const int64_t* tv; /* TC_REQ_LOCAL: device int64[n] */
+  const double* cc;  /* TC_REQ_LOCAL: device double[n] */
+  const int32_t* tri;/* TC_REQ_LIST: device int32[triangles][3] */
+  double queue_ms;   /* submit -> admitted */
+  double latency_ms; /* submit -> result ready */
+} tc_result;
+
+typedef struct {
+  int64_t admitted, completed, rejected, pending, running;
+  size_t pool_used, pool_capacity;
+  int64_t edges_done; /* oriented edges of the graphs of completed requests */
+} tc_serve_stats_t;
+
+/* Create a server on CUDA device `device` using the caller's device pool (>= 64 KiB). */
+tc_status tc_serve_create(int device, const tc_serve_config* cfg, void* pool_dev, size_t pool_bytes,
+                          tc_server** out);
+/* Stop the worker, wait for the slots and free the server (the pool stays the caller's). */
+void tc_serve_destroy(tc_server* s);
+const char* tc_serve_last_error(const tc_server* s);
+/*
+ * Copy an edge list (host int32[m][2], the input of tc_orient) to the device,
+ * orient it (Eq. (1), Figure 2 preprocessing) and keep the CSR resident.
+ * Blocks until the graph is ready; writes its id.
+ */
+tc_status tc_serve_add_graph(tc_server* s, int32_t n, int64_t m, const int32_t* edges_host, int64_t* graph_id);
+/* Free a resident graph (TC_ERR_NOT_READY while requests on it are unfinished). */
+tc_status tc_serve_remove_graph(tc_server* s, int64_t graph_id);
+/* Queue a request (tc_request_kind) on a resident graph; writes its ticket. */
+tc_status tc_serve_submit(tc_server* s, int64_t graph_id, int kind, int64_t* ticket);
+/* Result of a finished request, or TC_ERR_NOT_READY. */
+tc_status tc_serve_poll(tc_server* s, int64_t ticket, tc_result* out);
+/* Wait up to timeout_ms for a request; TC_ERR_TIMEOUT if it is still unfinished. */
+tc_status tc_serve_wait(tc_server* s, int64_t ticket, int64_t timeout_ms, tc_result* out);
+/* Drop a finished request and the device memory of its result. */
+tc_status tc_serve_release(tc_server* s, int64_t ticket);
+tc_status tc_serve_stats(tc_server* s, tc_serve_stats_t* out);
+
 /* ---- counting without allocation --------------------------------------- */
 
 /*

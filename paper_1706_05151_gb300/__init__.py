@@ -34,7 +34,9 @@ STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_INVALID_GRAPH", 3: "TC
 EXPORTS = ["tc_ctx_create", "tc_ctx_destroy", "tc_ctx_set_async", "tc_ctx_status", "tc_status_string",
            "tc_last_error", "tc_ctx_sm_count", "tc_version", "tc_workspace_size", "tc_orient", "tc_count",
            "tc_count_local", "tc_list_count", "tc_list_write", "tc_list", "tc_analyze", "tc_sparsify_count",
-           "tc_batch",
+           "tc_batch", "tc_serve_create", "tc_serve_destroy", "tc_serve_last_error", "tc_serve_add_graph",
+           "tc_serve_remove_graph", "tc_serve_submit", "tc_serve_poll", "tc_serve_wait", "tc_serve_release",
+           "tc_serve_stats",
            "tc_ctx_set_profiling", "tc_ctx_stage_count", "tc_ctx_stage", "tc_ctx_reset_stats", "tc_ctx_launches",
            "tc_count_static"]
 
@@ -43,6 +45,24 @@ class TcError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS.get(status, status)}: {message}")
         self.status = status
+
+
+class TcResult(ctypes.Structure):
+    """Mirror of the C struct tc_result."""
+    _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_int32), ("graph_id", ctypes.c_int64),
+                ("n", ctypes.c_int32), ("triangles", ctypes.c_uint64), ("tv", ctypes.c_void_p),
+                ("cc", ctypes.c_void_p), ("tri", ctypes.c_void_p), ("queue_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
+
+
+class TcServeConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("admit_timeout_ms", ctypes.c_int64)]
+
+
+class TcServeStats(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("pending", ctypes.c_int64), ("running", ctypes.c_int64), ("pool_used", ctypes.c_size_t),
+                ("pool_capacity", ctypes.c_size_t), ("edges_done", ctypes.c_int64)]
 
 
 class TcGraph(ctypes.Structure):
@@ -86,6 +106,16 @@ def load_library(path: str = LIB_PATH):
             "tc_analyze": (i32, [vp, G, vp, vp, vp, vp, i64, ctypes.POINTER(i64), vp, sz, vp]),
             "tc_batch": (i32, [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
             "tc_sparsify_count": (i32, [vp, G, ctypes.c_double, u64, vp, vp, vp, sz, vp]),
+            "tc_serve_create": (i32, [ctypes.c_int, ctypes.POINTER(TcServeConfig), vp, sz, ctypes.POINTER(vp)]),
+            "tc_serve_destroy": (None, [vp]),
+            "tc_serve_last_error": (ctypes.c_char_p, [vp]),
+            "tc_serve_add_graph": (i32, [vp, i32, i64, vp, ctypes.POINTER(i64)]),
+            "tc_serve_remove_graph": (i32, [vp, i64]),
+            "tc_serve_submit": (i32, [vp, i64, ctypes.c_int, ctypes.POINTER(i64)]),
+            "tc_serve_poll": (i32, [vp, i64, ctypes.POINTER(TcResult)]),
+            "tc_serve_wait": (i32, [vp, i64, i64, ctypes.POINTER(TcResult)]),
+            "tc_serve_release": (i32, [vp, i64]),
+            "tc_serve_stats": (i32, [vp, ctypes.POINTER(TcServeStats)]),
             "tc_ctx_set_profiling": (i32, [vp, ctypes.c_int]),
             "tc_ctx_stage_count": (ctypes.c_int, [vp]),
             "tc_ctx_stage": (i32, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
@@ -354,6 +384,122 @@ def batch(b: Batch, local: bool = True, ctx: Context | None = None):
                                _ptr(offsets), _ptr(cols), _ptr(deg), _ptr(dhat), _ptr(totals), _ptr(tv),
                                _ptr(ws), ws.numel(), _stream(dev)))
     return totals, (tv[:N] if tv is not None else None), Graph(N, E, offsets, cols[:E], deg[:N], dhat[:N])
+
+
+class _DeviceArray:
+    """A zero-copy view of device memory for torch.as_tensor (CUDA array interface)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, True),
+                                         "version": 3, "strides": None}
+
+
+COUNT, LOCAL, LIST = 0, 1, 2
+
+
+@dataclass
+class ServeResult:
+    ticket: int
+    status: int
+    kind: int
+    graph_id: int
+    triangles: int
+    queue_ms: float
+    latency_ms: float
+    tv: torch.Tensor | None = None
+    cc: torch.Tensor | None = None
+    tri: torch.Tensor | None = None
+
+
+class Server:
+    """tc_serve_*: a continuous-batching request server over resident graphs.
+
+    The device pool (pool_bytes of HBM) is allocated here with PyTorch and
+    handed to the server, which takes every device byte it uses from it.
+    """
+
+    def __init__(self, pool_bytes: int, slots: int = 8, device: int = 0, admit_timeout_ms: int = 10000):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libtc needs a CUDA GPU; none is available (there is no CPU fallback)")
+        self.lib = load_library()
+        self.device = torch.device("cuda", device)
+        self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=self.device)
+        torch.cuda.synchronize(self.device)
+        h = vp()
+        cfg = TcServeConfig(slots, admit_timeout_ms)
+        st = self.lib.tc_serve_create(device, ctypes.byref(cfg), _ptr(self.pool), self.pool.numel(), ctypes.byref(h))
+        if st != 0:
+            raise TcError(st, "tc_serve_create failed")
+        self.handle = h
+        self.edges_of = {}
+
+    def _check(self, st: int):
+        if st != 0:
+            raise TcError(st, self.lib.tc_serve_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.tc_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_graph(self, n: int, edges) -> int:
+        import numpy as np
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        gid = i64(0)
+        self._check(self.lib.tc_serve_add_graph(self.handle, int(n), len(e), e.ctypes.data_as(vp) if len(e) else None,
+                                                ctypes.byref(gid)))
+        self.edges_of[int(gid.value)] = len(e)
+        return int(gid.value)
+
+    def remove_graph(self, graph_id: int):
+        self._check(self.lib.tc_serve_remove_graph(self.handle, int(graph_id)))
+
+    def submit(self, graph_id: int, kind: int) -> int:
+        t = i64(0)
+        self._check(self.lib.tc_serve_submit(self.handle, int(graph_id), int(kind), ctypes.byref(t)))
+        return int(t.value)
+
+    def _result(self, ticket: int, r: TcResult, copy: bool) -> ServeResult:
+        out = ServeResult(ticket, r.status, r.kind, r.graph_id, int(r.triangles), r.queue_ms, r.latency_ms)
+        if copy and r.status == 0:
+            if r.tv:
+                out.tv = torch.as_tensor(_DeviceArray(r.tv, (r.n,), "<i8"), device=self.device).clone()
+                out.cc = torch.as_tensor(_DeviceArray(r.cc, (r.n,), "<f8"), device=self.device).clone()
+            if r.tri and r.triangles:
+                out.tri = torch.as_tensor(_DeviceArray(r.tri, (int(r.triangles), 3), "<i4"),
+                                          device=self.device).clone()
+            elif r.kind == LIST:
+                out.tri = torch.empty((0, 3), dtype=torch.int32, device=self.device)
+        return out
+
+    def wait(self, ticket: int, timeout_ms: int = 60000, copy: bool = True, release: bool = True) -> ServeResult:
+        r = TcResult()
+        st = self.lib.tc_serve_wait(self.handle, int(ticket), int(timeout_ms), ctypes.byref(r))
+        if st == 7:
+            raise TcError(st, "request still running")
+        res = self._result(ticket, r, copy)
+        if release:
+            self._check(self.lib.tc_serve_release(self.handle, int(ticket)))
+        return res
+
+    def poll(self, ticket: int):
+        r = TcResult()
+        st = self.lib.tc_serve_poll(self.handle, int(ticket), ctypes.byref(r))
+        return st, (self._result(ticket, r, False) if st != 9 else None)
+
+    def release(self, ticket: int):
+        self._check(self.lib.tc_serve_release(self.handle, int(ticket)))
+
+    def stats(self) -> dict:
+        s = TcServeStats()
+        self._check(self.lib.tc_serve_stats(self.handle, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in TcServeStats._fields_}
 
 
 def graph_from_csr(offsets: torch.Tensor, cols: torch.Tensor, deg=None, dhat=None) -> Graph:

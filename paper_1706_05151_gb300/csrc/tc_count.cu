@@ -543,14 +543,18 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
                                      {"local.tile", "local.block"},
                                      {"list_count.tile", "list_count.block"},
                                      {"list_write.tile", "list_write.block"}};
-  const int tgrid = persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_tile<MODE>), kTileWarps * 32, 0);
+  // persistent grids, but no more blocks than there is work for (small graphs leave room for other streams)
+  const int tgrid = static_cast<int>(min64(
+      persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_tile<MODE>), kTileWarps * 32, 0),
+      max64(1, (static_cast<int64_t>(a.n) + 32 * kTileWarps - 1) / (32 * kTileWarps))));
   {
     Stage st(ctx, s, kNames[MODE][0]);
     k_count_tile<MODE><<<tgrid, kTileWarps * 32, 0, s>>>(a, ws, ctx->d_err);
   }
   const size_t smem = sizeof(int32_t) * kBlockCap + (size_t(1) << kBlockBitsLog2) / 8;
-  const int bgrid =
-      persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_block<MODE>), kBlockWarps * 32, smem);
+  const int bgrid = static_cast<int>(min64(
+      persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_block<MODE>), kBlockWarps * 32, smem),
+      max64(1, a.m / (kTile + 1))));  // at most m / (kTile + 1) lists are longer than a tile
   {
     Stage st(ctx, s, kNames[MODE][1]);
     k_count_block<MODE><<<bgrid, kBlockWarps * 32, smem, s>>>(a, ws, ctx->d_err);
