@@ -43,6 +43,7 @@ WORKLOADS = {
     "er": dict(kind="er", n=16384, draws=131072, label="Erdos-Renyi G(n=16384, M=131072 draws)"),
     "ba22": dict(kind="ba", n=1 << 22, k=16, label="preferential attachment PA(n=2^22, k=16)"),
     "rmat22": dict(kind="rmat", scale=22, ef=16, label="R-MAT scale 22, edge factor 16 (0.57/0.19/0.19/0.05)"),
+    "rmat20": dict(kind="rmat", scale=20, ef=16, label="R-MAT scale 20, edge factor 16 (0.57/0.19/0.19/0.05)"),
 }
 
 

@@ -135,7 +135,13 @@ struct tc_server {
   Pool pool;
   std::mutex admin_mu;  // one graph is added at a time (admin stream and its error word)
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_done;
+  // wake-ups of the worker: completions (from stream host functions) and
+  // submissions bump `kicks` under wake_mu, which is never held across a CUDA
+  // call, so a host function can always take it
+  std::mutex wake_mu;
+  std::condition_variable cv_wake;
+  uint64_t kicks = 0;
   std::thread worker;
   bool stop = false;
   std::vector<Slot*> slots;
@@ -160,10 +166,18 @@ tc_status set_error(tc_server* s, tc_status st, const char* msg) {
   return st;
 }
 
+void kick(tc_server* s) {
+  {
+    std::lock_guard<std::mutex> g(s->wake_mu);
+    ++s->kicks;
+  }
+  s->cv_wake.notify_all();
+}
+
 void CUDART_CB on_slot_done(void* p) {
   auto* pr = static_cast<std::pair<tc_server*, Slot*>*>(p);
   pr->second->done.store(true, std::memory_order_release);
-  pr->first->cv_work.notify_all();
+  kick(pr->first);
   delete pr;
 }
 
@@ -259,8 +273,14 @@ bool anything_running(tc_server* s) {
 
 void worker_loop(tc_server* s) {
   cudaSetDevice(s->device);
-  std::unique_lock<std::mutex> lk(s->mu);
-  while (!s->stop) {
+  uint64_t seen = 0;
+  for (;;) {
+    {
+      std::lock_guard<std::mutex> g(s->wake_mu);
+      seen = s->kicks;
+    }
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->stop) break;
     bool progressed = false;
     // 1. retire finished slots
     for (size_t i = 0; i < s->slots.size(); ++i) {
@@ -351,7 +371,11 @@ void worker_loop(tc_server* s) {
       it = s->pending.erase(it);
       if (launch_request(s, r, g) != cudaSuccess) finish_request(s, r, TC_ERR_CUDA);
     }
-    if (!progressed) s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+    lk.unlock();
+    if (!progressed) {  // sleep until a completion or submission (or a timeout check is due)
+      std::unique_lock<std::mutex> g(s->wake_mu);
+      s->cv_wake.wait_for(g, std::chrono::milliseconds(20), [&] { return s->kicks != seen; });
+    }
   }
 }
 
@@ -411,7 +435,7 @@ void tc_serve_destroy(tc_server* s) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
   }
-  s->cv_work.notify_all();
+  kick(s);
   if (s->worker.joinable()) s->worker.join();
   cudaSetDevice(s->device);
   for (Slot* sl : s->slots) {
@@ -517,7 +541,7 @@ tc_status tc_serve_submit(tc_server* s, int64_t graph_id, int kind, int64_t* tic
     s->pending.push_back(r.ticket);
     *ticket = r.ticket;
   }
-  s->cv_work.notify_all();
+  kick(s);
   return TC_OK;
 }
 
@@ -564,14 +588,16 @@ tc_status tc_serve_wait(tc_server* s, int64_t ticket, int64_t timeout_ms, tc_res
 
 tc_status tc_serve_release(tc_server* s, int64_t ticket) {
   if (!s) return TC_ERR_INVALID_ARG;
-  std::lock_guard<std::mutex> lk(s->mu);
-  auto it = s->reqs.find(ticket);
-  if (it == s->reqs.end()) return TC_ERR_INVALID_ARG;
-  if (it->second.state != REQ_DONE) return TC_ERR_NOT_READY;
-  s->pool.release(it->second.out);
-  s->pool.release(it->second.tri);
-  s->reqs.erase(it);
-  s->cv_work.notify_all();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return TC_ERR_INVALID_ARG;
+    if (it->second.state != REQ_DONE) return TC_ERR_NOT_READY;
+    s->pool.release(it->second.out);
+    s->pool.release(it->second.tri);
+    s->reqs.erase(it);
+  }
+  kick(s);  // freed memory may admit a waiting request
   return TC_OK;
 }
 
