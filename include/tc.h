@@ -104,6 +104,16 @@ int tc_ctx_sm_count(const tc_ctx* ctx);
 const char* tc_version(void);
 
 /*
+ * Tuning (no counterpart in the paper; the paper balances processors with the
+ * cost functions of Table "lbscheme", this balances one GPU).  tile_max: apex
+ * vertices with |N_v| > tile_max are counted one thread block per vertex, the
+ * others 32 to a warp (0 = 512, the largest allowed).  grid_div: persistent
+ * grids use 1/grid_div of the GPU's resident capacity (0 or 1 = all of it),
+ * leaving room for work on other streams.  Results do not depend on either.
+ */
+tc_status tc_ctx_set_tuning(tc_ctx* ctx, int32_t tile_max, int32_t grid_div);
+
+/*
  * Per-stage timing and launch accounting (no counterpart in the paper; it
  * measures this library).  With profiling on, each kernel group a call
  * launches is bracketed by CUDA events on the call's stream; the totals are
@@ -284,6 +294,8 @@ typedef enum {
 typedef struct {
   int32_t slots;            /* requests on the GPU at once (0 = 8, at most 64) */
   int64_t admit_timeout_ms; /* how long a request may wait for memory before TC_ERR_REJECTED (0 = 10 s) */
+  int32_t grid_div;         /* each request's persistent grids use 1/grid_div of the GPU (0 = 2) */
+  int32_t tile_max;         /* as tc_ctx_set_tuning (0 = default) */
 } tc_serve_config;
 
 typedef struct {

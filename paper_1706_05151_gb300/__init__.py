@@ -37,7 +37,7 @@ EXPORTS = ["tc_ctx_create", "tc_ctx_destroy", "tc_ctx_set_async", "tc_ctx_status
            "tc_batch", "tc_serve_create", "tc_serve_destroy", "tc_serve_last_error", "tc_serve_add_graph",
            "tc_serve_remove_graph", "tc_serve_submit", "tc_serve_poll", "tc_serve_wait", "tc_serve_release",
            "tc_serve_stats",
-           "tc_ctx_set_profiling", "tc_ctx_stage_count", "tc_ctx_stage", "tc_ctx_reset_stats", "tc_ctx_launches",
+           "tc_ctx_set_tuning", "tc_ctx_set_profiling", "tc_ctx_stage_count", "tc_ctx_stage", "tc_ctx_reset_stats", "tc_ctx_launches",
            "tc_count_static"]
 
 
@@ -56,7 +56,8 @@ class TcResult(ctypes.Structure):
 
 
 class TcServeConfig(ctypes.Structure):
-    _fields_ = [("slots", ctypes.c_int32), ("admit_timeout_ms", ctypes.c_int64)]
+    _fields_ = [("slots", ctypes.c_int32), ("admit_timeout_ms", ctypes.c_int64), ("grid_div", ctypes.c_int32),
+                ("tile_max", ctypes.c_int32)]
 
 
 class TcServeStats(ctypes.Structure):
@@ -116,6 +117,7 @@ def load_library(path: str = LIB_PATH):
             "tc_serve_wait": (i32, [vp, i64, i64, ctypes.POINTER(TcResult)]),
             "tc_serve_release": (i32, [vp, i64]),
             "tc_serve_stats": (i32, [vp, ctypes.POINTER(TcServeStats)]),
+            "tc_ctx_set_tuning": (i32, [vp, i32, i32]),
             "tc_ctx_set_profiling": (i32, [vp, ctypes.c_int]),
             "tc_ctx_stage_count": (ctypes.c_int, [vp]),
             "tc_ctx_stage": (i32, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
@@ -178,6 +180,10 @@ class Context:
 
     def status(self):
         self.check(self.lib.tc_ctx_status(self.handle, _stream(self.device)))
+
+    def set_tuning(self, tile_max: int = 0, grid_div: int = 1):
+        """tc_ctx_set_tuning: tile/block threshold on |N_v| and the share of the GPU per launch."""
+        self.check(self.lib.tc_ctx_set_tuning(self.handle, int(tile_max), int(grid_div)))
 
     def set_profiling(self, on: bool):
         self.check(self.lib.tc_ctx_set_profiling(self.handle, 1 if on else 0))
@@ -418,7 +424,8 @@ class Server:
     handed to the server, which takes every device byte it uses from it.
     """
 
-    def __init__(self, pool_bytes: int, slots: int = 8, device: int = 0, admit_timeout_ms: int = 10000):
+    def __init__(self, pool_bytes: int, slots: int = 8, device: int = 0, admit_timeout_ms: int = 10000,
+                 grid_div: int = 2, tile_max: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("libtc needs a CUDA GPU; none is available (there is no CPU fallback)")
         self.lib = load_library()
@@ -426,7 +433,7 @@ class Server:
         self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=self.device)
         torch.cuda.synchronize(self.device)
         h = vp()
-        cfg = TcServeConfig(slots, admit_timeout_ms)
+        cfg = TcServeConfig(slots, admit_timeout_ms, grid_div, tile_max)
         st = self.lib.tc_serve_create(device, ctypes.byref(cfg), _ptr(self.pool), self.pool.numel(), ctypes.byref(h))
         if st != 0:
             raise TcError(st, "tc_serve_create failed")

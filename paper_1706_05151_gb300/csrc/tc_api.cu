@@ -206,6 +206,13 @@ tc_status tc_ctx_status(tc_ctx* ctx, tc_stream stream) {
   return status_from_bits(ctx, *ctx->h_err);
 }
 
+tc_status tc_ctx_set_tuning(tc_ctx* ctx, int32_t tile_max, int32_t grid_div) {
+  if (!ctx || tile_max < 0 || tile_max > 512 || grid_div < 0 || grid_div > 64) return TC_ERR_INVALID_ARG;
+  ctx->tile_max = tile_max;
+  ctx->grid_div = grid_div > 0 ? grid_div : 1;
+  return TC_OK;
+}
+
 tc_status tc_ctx_set_profiling(tc_ctx* ctx, int on) {
   if (!ctx) return TC_ERR_INVALID_ARG;
   ctx->prof.on = on != 0;

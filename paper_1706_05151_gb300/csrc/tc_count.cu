@@ -37,8 +37,7 @@ constexpr int kTile = 512;           // ids staged per warp; longer lists go to 
 constexpr int kTileWarps = 4;        // warps per block, tile kernel
 constexpr int kTileBitsLog2 = 14;    // filter bits per tile (2 KB): <= 512 / 16384 false positives
 constexpr int kUnroll = 4;           // candidate windows in flight per lane
-constexpr int kShortLen = 32;        // N_u shorter than this is walked end to end with others
-constexpr int kOwnCap = 32 * kShortLen;
+constexpr int kShortLen = 32;        // N_u of at most this many ids: half a warp per edge, two windows
 constexpr int kBlockCap = 4096;      // ids of N_v staged per pass, block kernel
 constexpr int kBlockBitsLog2 = 16;   // filter bits per staged chunk (8 KB)
 constexpr int kBlockWarps = 8;       // warps per block, block kernel
@@ -140,7 +139,6 @@ struct BatchSmem {
   uint32_t cnt[32];       // matches of the edge
   int32_t qw[64];         // filter survivors: candidate id ...
   int32_t qs[64];         // ... and its edge
-  uint8_t own[kOwnCap];   // flattened position -> edge, short lists
 };
 
 struct Probe {            // what the candidates are tested against
@@ -256,44 +254,47 @@ __device__ __forceinline__ uint32_t process_batch(BatchSmem& bs, const Probe& pr
   int64_t ub = 0;
   int32_t len = 0;
   if (act) len = list_bounds(a, u, ub, err);
-  const bool is_short = len < kShortLen;
-  const int32_t slen = is_short ? len : 0;
-  const int32_t incl = warp_incl_scan(slen);
-  const int32_t tot = __shfl_sync(FULL, incl, 31);
-  const int32_t excl = incl - slen;
+  const int32_t slen = len <= kShortLen ? len : 0;
   __syncwarp();
-  bs.beg[lane] = is_short ? ub - excl : ub;
+  bs.beg[lane] = ub;
   bs.u[lane] = u;
   bs.lo[lane] = lo;
   bs.len[lane] = vlen;
   bs.salt[lane] = salt;
   bs.cnt[lane] = 0;
-  for (int i = 0; i < slen; ++i) bs.own[excl + i] = static_cast<uint8_t>(lane);
   __syncwarp();
   int qn = 0;
-  // short lists, end to end
-  for (int32_t p0 = 0; p0 < tot; p0 += 32 * kUnroll) {
-    int32_t w[kUnroll];
-    int s[kUnroll];
+  // short lists: half a warp per edge, edges 2i and 2i+1 side by side, two
+  // pairs (eight loads) in flight
+  if (__any_sync(FULL, slen > 0)) {
+    const int half = lane >> 4, hl = lane & 15;
+    for (int pi = 0; pi < 16; pi += 2) {
+      int32_t le[2], lmax[2], se[2], w[4];
+      int64_t b[2];
 #pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
-      const int32_t p = p0 + 32 * k + lane;
-      s[k] = 0;
-      w[k] = 0;
-      if (p < tot) {
-        s[k] = bs.own[p];
-        w[k] = a.cols[bs.beg[s[k]] + p];
+      for (int k = 0; k < 2; ++k) {
+        const int e = 2 * (pi + k) + half;
+        le[k] = __shfl_sync(FULL, slen, e);
+        lmax[k] = max(le[k], __shfl_xor_sync(FULL, le[k], 16));
+        b[k] = __shfl_sync(FULL, ub, e);
+        se[k] = __shfl_sync(FULL, salt, e);
+        w[2 * k] = hl < le[k] ? a.cols[b[k] + hl] : 0;
+        w[2 * k + 1] = hl + 16 < le[k] ? a.cols[b[k] + hl + 16] : 0;
       }
-    }
 #pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
-      const int32_t p = p0 + 32 * k + lane;
-      const bool pass = p < tot && passes<TILE>(pr, bs.salt[s[k]], w[k]);
-      push<MODE, TILE>(bs, pr, pass, w[k], s[k], qn, vbase_or_v, vrun, cursor, a, ws, err);
+      for (int k = 0; k < 2; ++k) {
+        const int e = 2 * (pi + k) + half;
+        if (lmax[k] > 0)
+          push<MODE, TILE>(bs, pr, hl < le[k] && passes<TILE>(pr, se[k], w[2 * k]), w[2 * k], e, qn, vbase_or_v,
+                           vrun, cursor, a, ws, err);
+        if (lmax[k] > 16)
+          push<MODE, TILE>(bs, pr, hl + 16 < le[k] && passes<TILE>(pr, se[k], w[2 * k + 1]), w[2 * k + 1], e, qn,
+                           vbase_or_v, vrun, cursor, a, ws, err);
+      }
     }
   }
   // long lists, one edge at a time
-  unsigned lm = __ballot_sync(FULL, act && !is_short);
+  unsigned lm = __ballot_sync(FULL, len > kShortLen);
   while (lm) {
     const int e = __ffs(lm) - 1;
     lm &= lm - 1;
@@ -376,7 +377,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, Cou
     const int64_t d = e - b;
     // the listing write pass only revisits apex vertices that have triangles
     const bool skip = MODE == MODE_LIST_WRITE && valid && ws.vcount[v] == 0;
-    const bool big = valid && !skip && d > kTile;
+    const bool big = valid && !skip && d > a.tile_max;
     const unsigned bigmask = __ballot_sync(FULL, big);
     if (bigmask) {
       uint32_t qb = 0;
@@ -554,7 +555,7 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
   const size_t smem = sizeof(int32_t) * kBlockCap + (size_t(1) << kBlockBitsLog2) / 8;
   const int bgrid = static_cast<int>(min64(
       persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_block<MODE>), kBlockWarps * 32, smem),
-      max64(1, a.m / (kTile + 1))));  // at most m / (kTile + 1) lists are longer than a tile
+      max64(1, a.m / (a.tile_max + 1))));  // at most m / (tile_max + 1) lists go to this kernel
   {
     Stage st(ctx, s, kNames[MODE][1]);
     k_count_block<MODE><<<bgrid, kBlockWarps * 32, smem, s>>>(a, ws, ctx->d_err);
@@ -582,13 +583,16 @@ int persistent_blocks(Ctx* ctx, const void* kernel, int threads, size_t dyn_smem
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, dyn_smem) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
-  return per_sm * ctx->sm_count;
+  const int div = ctx->grid_div > 1 ? ctx->grid_div : 1;
+  return static_cast<int>(max64(ctx->sm_count, static_cast<int64_t>(per_sm) * ctx->sm_count / div));
 }
 
-cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a, CountWs ws, cudaStream_t s) {
+cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a_in, CountWs ws, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(ws.counters, 0, sizeof(uint32_t) * 4, s);
   if (e != cudaSuccess) return e;
-  if (a.n <= 0) return cudaGetLastError();
+  if (a_in.n <= 0) return cudaGetLastError();
+  CountArgs a = a_in;
+  a.tile_max = (ctx->tile_max > 0 && ctx->tile_max < kTile) ? ctx->tile_max : kTile;
   switch (mode) {
     case MODE_COUNT: return launch_mode<MODE_COUNT>(ctx, a, ws, s);
     case MODE_LOCAL: return launch_mode<MODE_LOCAL>(ctx, a, ws, s);

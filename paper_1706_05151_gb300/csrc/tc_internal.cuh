@@ -53,6 +53,8 @@ struct Ctx {
   uint32_t* d_err = nullptr;  // device error word
   uint32_t* h_err = nullptr;  // pinned host mirror
   int64_t launches = 0;       // kernels this context has launched
+  int32_t tile_max = 0;       // tuning: longest N_v counted by the tile kernel (0 = its capacity)
+  int32_t grid_div = 1;       // tuning: persistent grids use 1/grid_div of the resident capacity
   Profiler prof;
   char last_error[256] = {0};
 };
@@ -156,6 +158,7 @@ struct CountArgs {
   int64_t cap;                // MODE_LIST_WRITE
   unsigned long long* graph_total = nullptr;  // batched form: T per graph ...
   const int32_t* gid = nullptr;               // ... indexed by the graph id of the apex vertex
+  int32_t tile_max = 0;                       // lists longer than this go to the block kernel (set by launch_count)
 };
 cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a, CountWs ws, cudaStream_t s);
 cudaError_t launch_clustering(Ctx* ctx, int32_t n, const int32_t* deg, const int64_t* tv, double* cc, cudaStream_t s);

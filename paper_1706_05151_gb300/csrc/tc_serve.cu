@@ -390,6 +390,8 @@ tc_status tc_serve_create(int device, const tc_serve_config* cfg, void* pool_dev
   const int slots = cfg && cfg->slots > 0 ? cfg->slots : 8;
   if (slots > 64) return TC_ERR_INVALID_ARG;
   const int64_t admit_timeout = cfg && cfg->admit_timeout_ms > 0 ? cfg->admit_timeout_ms : 10000;
+  const int32_t grid_div = cfg && cfg->grid_div > 0 ? cfg->grid_div : 2;
+  const int32_t tile_max = cfg && cfg->tile_max > 0 ? cfg->tile_max : 0;
   if (cudaSetDevice(device) != cudaSuccess) return TC_ERR_CUDA;
   tc_server* s = new tc_server();
   s->device = device;
@@ -420,6 +422,8 @@ tc_status tc_serve_create(int device, const tc_serve_config* cfg, void* pool_dev
     sl->ctx.device = device;
     sl->ctx.sm_count = sms;
     sl->ctx.async = 1;
+    sl->ctx.grid_div = grid_div;
+    sl->ctx.tile_max = tile_max;
     sl->ctx.d_err = static_cast<uint32_t*>(sl->err_block);
     sl->ctx.h_err = reinterpret_cast<uint32_t*>(sl->h_total + 4);
   }

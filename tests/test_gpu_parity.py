@@ -265,3 +265,42 @@ def test_broken_csr_is_reported_not_read(tc):
     with pytest.raises(tc.TcError) as ex:
         tc.count(g2)
     assert ex.value.status == 2
+
+
+# ---- tuning never changes results ---------------------------------------------------
+
+@pytest.mark.parametrize("make", [
+    lambda: (1 << 14, synth.rmat(14, 16, 40)),
+    lambda: (700, synth.complete(700)),
+    lambda: (20000, synth.chung_lu(20000, 48.0, 2.1, 41, 0)),
+])
+def test_results_independent_of_tuning(tc, make):
+    n, e = make()
+    ctx = tc.default_context()
+    g = tc.orient(to_dev(e), n)
+    ref = oracle.count(n, e, local=True)
+    try:
+        for tile_max, grid_div in [(32, 1), (128, 3), (512, 1), (1, 2)]:
+            ctx.set_tuning(tile_max, grid_div)
+            T, tv, cc, tri = tc.analyze(g)
+            assert T == ref["T"] and np.array_equal(tv.cpu().numpy(), ref["tv"])
+            assert len(tri) == T
+            assert tc.count(g) == T
+            assert tc.sparsify_count(g, 0.3, 5)[:2] == oracle.sparsify_count(n, e, 5, 0.3)[:2]
+    finally:
+        ctx.set_tuning(0, 1)
+
+
+def test_autotuner_records_a_candidate(tc, tmp_path):
+    from paper_1706_05151_gb300 import autotune
+    n = 1 << 13
+    g = tc.orient(to_dev(synth.rmat(13, 16, 42)), n)
+    path = str(tmp_path / "tuning.json")
+    try:
+        best, times = autotune.tune(g, repeats=1, path=path)
+        assert best in autotune.CANDIDATES and set(times) == set(autotune.CANDIDATES)
+        assert autotune.apply(g, path=path) == best
+        assert autotune.shape_class(g) in autotune.load_table(path)
+        assert tc.count(g) == oracle.count(n, synth.rmat(13, 16, 42))["T"]
+    finally:
+        tc.default_context().set_tuning(0, 1)
