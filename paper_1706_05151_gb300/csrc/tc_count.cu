@@ -37,9 +37,8 @@ constexpr int kTile = 512;           // ids staged per warp; longer lists go to 
 constexpr int kTileWarps = 4;        // warps per block, tile kernel
 constexpr int kTileBitsLog2 = 14;    // filter bits per tile (2 KB): <= 512 / 16384 false positives
 constexpr int kUnroll = 4;           // candidate windows in flight per lane
-constexpr int kShortLen = 32;        // N_u of at most this many ids: half a warp per edge, two windows
-constexpr int kBlockCap = 4096;      // ids of N_v staged per pass, block kernel
-constexpr int kBlockBitsLog2 = 16;   // filter bits per staged chunk (8 KB)
+constexpr int kShortLen = 32;        // N_u shorter than this is walked end to end with others
+constexpr int kOwnCap = 32 * kShortLen;
 constexpr int kBlockWarps = 8;       // warps per block, block kernel
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
@@ -139,6 +138,7 @@ struct BatchSmem {
   uint32_t cnt[32];       // matches of the edge
   int32_t qw[64];         // filter survivors: candidate id ...
   int32_t qs[64];         // ... and its edge
+  uint8_t own[kOwnCap];   // flattened position -> edge, short lists
 };
 
 struct Probe {            // what the candidates are tested against
@@ -151,8 +151,7 @@ struct Probe {            // what the candidates are tested against
 
 template <bool TILE>
 __device__ __forceinline__ bool passes(const Probe& pr, int32_t salt, int32_t w) {
-  if (TILE) return ftest<kTileBitsLog2>(pr.bits, w, salt);
-  return w >= pr.lo && w <= pr.hi && ftest<kBlockBitsLog2>(pr.bits, w, 0);
+  return ftest<kTileBitsLog2>(pr.bits, w, salt);
 }
 
 // Exact check of the first `cnt` queued survivors, with the per-mode effects.
@@ -254,47 +253,44 @@ __device__ __forceinline__ uint32_t process_batch(BatchSmem& bs, const Probe& pr
   int64_t ub = 0;
   int32_t len = 0;
   if (act) len = list_bounds(a, u, ub, err);
-  const int32_t slen = len <= kShortLen ? len : 0;
+  const bool is_short = len < kShortLen;
+  const int32_t slen = is_short ? len : 0;
+  const int32_t incl = warp_incl_scan(slen);
+  const int32_t tot = __shfl_sync(FULL, incl, 31);
+  const int32_t excl = incl - slen;
   __syncwarp();
-  bs.beg[lane] = ub;
+  bs.beg[lane] = is_short ? ub - excl : ub;
   bs.u[lane] = u;
   bs.lo[lane] = lo;
   bs.len[lane] = vlen;
   bs.salt[lane] = salt;
   bs.cnt[lane] = 0;
+  for (int i = 0; i < slen; ++i) bs.own[excl + i] = static_cast<uint8_t>(lane);
   __syncwarp();
   int qn = 0;
-  // short lists: half a warp per edge, edges 2i and 2i+1 side by side, two
-  // pairs (eight loads) in flight
-  if (__any_sync(FULL, slen > 0)) {
-    const int half = lane >> 4, hl = lane & 15;
-    for (int pi = 0; pi < 16; pi += 2) {
-      int32_t le[2], lmax[2], se[2], w[4];
-      int64_t b[2];
+  // short lists, end to end
+  for (int32_t p0 = 0; p0 < tot; p0 += 32 * kUnroll) {
+    int32_t w[kUnroll];
+    int s[kUnroll];
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int e = 2 * (pi + k) + half;
-        le[k] = __shfl_sync(FULL, slen, e);
-        lmax[k] = max(le[k], __shfl_xor_sync(FULL, le[k], 16));
-        b[k] = __shfl_sync(FULL, ub, e);
-        se[k] = __shfl_sync(FULL, salt, e);
-        w[2 * k] = hl < le[k] ? a.cols[b[k] + hl] : 0;
-        w[2 * k + 1] = hl + 16 < le[k] ? a.cols[b[k] + hl + 16] : 0;
+    for (int k = 0; k < kUnroll; ++k) {
+      const int32_t p = p0 + 32 * k + lane;
+      s[k] = 0;
+      w[k] = 0;
+      if (p < tot) {
+        s[k] = bs.own[p];
+        w[k] = a.cols[bs.beg[s[k]] + p];
       }
+    }
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int e = 2 * (pi + k) + half;
-        if (lmax[k] > 0)
-          push<MODE, TILE>(bs, pr, hl < le[k] && passes<TILE>(pr, se[k], w[2 * k]), w[2 * k], e, qn, vbase_or_v,
-                           vrun, cursor, a, ws, err);
-        if (lmax[k] > 16)
-          push<MODE, TILE>(bs, pr, hl + 16 < le[k] && passes<TILE>(pr, se[k], w[2 * k + 1]), w[2 * k + 1], e, qn,
-                           vbase_or_v, vrun, cursor, a, ws, err);
-      }
+    for (int k = 0; k < kUnroll; ++k) {
+      const int32_t p = p0 + 32 * k + lane;
+      const bool pass = p < tot && passes<TILE>(pr, bs.salt[s[k]], w[k]);
+      push<MODE, TILE>(bs, pr, pass, w[k], s[k], qn, vbase_or_v, vrun, cursor, a, ws, err);
     }
   }
   // long lists, one edge at a time
-  unsigned lm = __ballot_sync(FULL, len > kShortLen);
+  unsigned lm = __ballot_sync(FULL, act && !is_short);
   while (lm) {
     const int e = __ffs(lm) - 1;
     lm &= lm - 1;
@@ -462,15 +458,142 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, Cou
 }
 
 // ---------------------------------------------------------------------------
-// Block kernel (lists longer than kTile)
+// Block kernel (lists longer than tile_max).  Heavy apex vertices get a whole
+// block; N_v is hashed into a shared-memory open-addressing table (load factor
+// at most 1/4) so that membership is exact in about one probe, with no filter,
+// no survivor queue and no binary search.
 // ---------------------------------------------------------------------------
 
+constexpr int kHashSlotsLog2 = 13;                   // 8192 slots (32 KB)
+constexpr int kHashCap = (1 << kHashSlotsLog2) / 4;  // ids of N_v per pass
+
+__device__ __forceinline__ uint32_t slot_of(int32_t w) {
+  return (static_cast<uint32_t>(w) * 0x9E3779B1u) >> (32 - kHashSlotsLog2);
+}
+
+__device__ __forceinline__ bool hash_member(const int32_t* tab, int32_t w) {
+  if (w < 0) return false;
+  uint32_t h = slot_of(w);
+  for (int probe = 0; probe < (1 << kHashSlotsLog2); ++probe) {  // bounded: the table is never full
+    const int32_t x = tab[h];
+    if (x == w) return true;
+    if (x < 0) return false;
+    h = (h + 1) & ((1u << kHashSlotsLog2) - 1);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void hash_insert(int32_t* tab, int32_t w) {
+  uint32_t h = slot_of(w);
+  for (int probe = 0; probe < (1 << kHashSlotsLog2); ++probe) {
+    const int32_t prev = atomicCAS(&tab[h], -1, w);
+    if (prev == -1 || prev == w) return;
+    h = (h + 1) & ((1u << kHashSlotsLog2) - 1);
+  }
+}
+
+struct HashBatch {
+  int64_t beg[32];        // short list: start of N_u minus its flattened offset; long list: start of N_u
+  int32_t u[32];
+  uint32_t cnt[32];       // matches of the edge
+  uint8_t own[kOwnCap];   // flattened position -> edge, short lists
+};
+
 template <int MODE>
-__global__ void __launch_bounds__(kBlockWarps * 32) k_count_block(CountArgs a, CountWs ws, uint32_t* err) {
-  extern __shared__ int32_t dyn[];
-  int32_t* sv = dyn;
-  uint32_t* bits = reinterpret_cast<uint32_t*>(dyn + kBlockCap);
-  __shared__ BatchSmem s_b[kBlockWarps];
+__device__ __forceinline__ void hash_record(HashBatch& hb, bool found, int32_t w, int s, int32_t v,
+                                            unsigned long long* cursor, const CountArgs& a, uint32_t* err) {
+  if (found) {
+    atomicAdd(&hb.cnt[s], 1u);
+    if (MODE == MODE_LOCAL) atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + w), 1ull);
+  }
+  if (MODE == MODE_LIST_WRITE) {
+    const unsigned fm = __ballot_sync(FULL, found);
+    if (fm) {
+      unsigned long long b0 = 0;
+      if (lane_id() == 0) b0 = atomicAdd(cursor, static_cast<unsigned long long>(__popc(fm)));
+      const int64_t base = static_cast<int64_t>(__shfl_sync(FULL, b0, 0));
+      if (found) {
+        const int64_t idx = base + __popc(fm & lanemask_lt());
+        if (idx < a.cap) {
+          a.tri[3 * idx] = v;
+          a.tri[3 * idx + 1] = hb.u[s];
+          a.tri[3 * idx + 2] = w;
+        } else {
+          set_err(err, ERR_CAPACITY);
+        }
+      }
+    }
+  }
+}
+
+// One batch of edges (v, u), u on this lane if `act`, against the hashed chunk
+// of N_v whose ids lie in [lo, hi].  Returns the matches of this lane's edge.
+template <int MODE>
+__device__ __forceinline__ uint32_t hash_batch(HashBatch& hb, const int32_t* tab, int32_t lo, int32_t hi, int32_t u,
+                                               bool act, int32_t v, unsigned long long* cursor, const CountArgs& a,
+                                               uint32_t* err) {
+  const int lane = lane_id();
+  int64_t ub = 0;
+  int32_t len = 0;
+  if (act) len = list_bounds(a, u, ub, err);
+  const bool is_short = len < kShortLen;
+  const int32_t slen = is_short ? len : 0;
+  const int32_t incl = warp_incl_scan(slen);
+  const int32_t tot = __shfl_sync(FULL, incl, 31);
+  const int32_t excl = incl - slen;
+  __syncwarp();
+  hb.beg[lane] = is_short ? ub - excl : ub;
+  hb.u[lane] = u;
+  hb.cnt[lane] = 0;
+  for (int i = 0; i < slen; ++i) hb.own[excl + i] = static_cast<uint8_t>(lane);
+  __syncwarp();
+  for (int32_t p0 = 0; p0 < tot; p0 += 32 * kUnroll) {
+    int32_t w[kUnroll];
+    int s[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      const int32_t p = p0 + 32 * k + lane;
+      s[k] = 0;
+      w[k] = -1;
+      if (p < tot) {
+        s[k] = hb.own[p];
+        w[k] = a.cols[hb.beg[s[k]] + p];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      const bool found = w[k] >= lo && w[k] <= hi && hash_member(tab, w[k]);
+      hash_record<MODE>(hb, found, w[k], s[k], v, cursor, a, err);
+    }
+  }
+  unsigned lm = __ballot_sync(FULL, act && !is_short);
+  while (lm) {
+    const int e = __ffs(lm) - 1;
+    lm &= lm - 1;
+    const int64_t b = hb.beg[e];
+    const int32_t le = __shfl_sync(FULL, len, e);
+    for (int32_t p0 = 0; p0 < le; p0 += 32 * kUnroll) {
+      int32_t w[kUnroll];
+#pragma unroll
+      for (int k = 0; k < kUnroll; ++k) {
+        const int32_t p = p0 + 32 * k + lane;
+        w[k] = p < le ? a.cols[b + p] : -1;
+      }
+#pragma unroll
+      for (int k = 0; k < kUnroll; ++k) {
+        const bool found = w[k] >= lo && w[k] <= hi && hash_member(tab, w[k]);
+        hash_record<MODE>(hb, found, w[k], e, v, cursor, a, err);
+      }
+    }
+  }
+  __syncwarp();
+  return act ? hb.cnt[lane] : 0u;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a, CountWs ws, uint32_t* err) {
+  extern __shared__ int32_t tab[];
+  __shared__ HashBatch s_hb[kBlockWarps];
   __shared__ unsigned long long s_red[kBlockWarps];
   __shared__ unsigned long long s_cursor;
   const int lane = lane_id(), wid = threadIdx.x >> 5;
@@ -482,29 +605,28 @@ __global__ void __launch_bounds__(kBlockWarps * 32) k_count_block(CountArgs a, C
     const int64_t dv = e - b;
     if (threadIdx.x == 0 && MODE == MODE_LIST_WRITE) s_cursor = static_cast<unsigned long long>(ws.voff[v]);
     unsigned long long cv = 0;
-    for (int64_t c0 = 0; c0 < dv; c0 += kBlockCap) {
-      const int clen = static_cast<int>(min64(kBlockCap, dv - c0));
+    for (int64_t c0 = 0; c0 < dv; c0 += kHashCap) {
+      const int clen = static_cast<int>(min64(kHashCap, dv - c0));
+      __syncthreads();
+      for (int i = threadIdx.x; i < (1 << kHashSlotsLog2); i += blockDim.x) tab[i] = -1;
       __syncthreads();
       bool bad = false;
       for (int i = threadIdx.x; i < clen; i += blockDim.x) {
         const int32_t x = a.cols[b + c0 + i];
-        sv[i] = x;
-        bad |= static_cast<uint32_t>(x) >= static_cast<uint32_t>(a.n);
+        if (static_cast<uint32_t>(x) >= static_cast<uint32_t>(a.n)) bad = true;
+        else hash_insert(tab, x);
       }
-      for (int i = threadIdx.x; i < (1 << kBlockBitsLog2) / 32; i += blockDim.x) bits[i] = 0u;
       if (__syncthreads_or(bad)) {
         if (threadIdx.x == 0) set_err(err, ERR_BAD_ID);
         break;
       }
-      for (int i = threadIdx.x; i < clen; i += blockDim.x) fset<kBlockBitsLog2>(bits, sv[i], 0);
-      __syncthreads();
-      const Probe pr{sv, bits, 1 << (31 - __clz(clen)), clen, sv[0], sv[clen - 1]};
+      // the chunk is a sorted run of N_v: its ids lie in [lo, hi]
+      const int32_t lo = a.cols[b + c0], hi = a.cols[b + c0 + clen - 1];
       for (int64_t ub = static_cast<int64_t>(wid) * 32; ub < dv; ub += kBlockWarps * 32) {
         const int nb = static_cast<int>(min64(32, dv - ub));
         const bool act = lane < nb;
         const int32_t u = act ? a.cols[b + ub + lane] : 0;
-        const uint32_t c =
-            process_batch<MODE, false>(s_b[wid], pr, u, act, 0, 0, 0, v, nullptr, &s_cursor, a, ws, err);
+        const uint32_t c = hash_batch<MODE>(s_hb[wid], tab, lo, hi, u, act, v, &s_cursor, a, err);
         cv += c;
         if (MODE == MODE_LOCAL && c)
           atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + u), static_cast<unsigned long long>(c));
@@ -552,7 +674,7 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
     Stage st(ctx, s, kNames[MODE][0]);
     k_count_tile<MODE><<<tgrid, kTileWarps * 32, 0, s>>>(a, ws, ctx->d_err);
   }
-  const size_t smem = sizeof(int32_t) * kBlockCap + (size_t(1) << kBlockBitsLog2) / 8;
+  const size_t smem = sizeof(int32_t) << kHashSlotsLog2;
   const int bgrid = static_cast<int>(min64(
       persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_block<MODE>), kBlockWarps * 32, smem),
       max64(1, a.m / (a.tile_max + 1))));  // at most m / (tile_max + 1) lists go to this kernel

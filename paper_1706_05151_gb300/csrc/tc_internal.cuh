@@ -24,6 +24,7 @@ enum : uint32_t {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kSortBlockCap = 32768;     // longest list tc_orient sorts (ints in shared memory)
+constexpr int kSortWarpCap = 1024;       // lists up to this length are sorted by one warp
 constexpr int kMaxListLen = 1 << 24;     // longest list the counting kernels accept
 
 // Optional per-stage timing: CUDA events recorded around each kernel group on
@@ -111,8 +112,9 @@ CountWs carve_count(Carver& c, int32_t n, bool listing);
 
 struct OrientWs {
   int32_t* cursor;      // fill cursor per vertex
-  int32_t* big_queue;   // vertices whose lists the block sorter takes
-  uint32_t* counters;   // [0] queue length
+  int32_t* big_queue;   // vertices whose lists the block sorter takes (> kSortWarpCap ids)
+  int32_t* mid_queue;   // vertices whose lists the warp sorter takes (33 .. kSortWarpCap ids)
+  uint32_t* counters;   // [0] big queue length, [1] mid queue length
   ScanWs scan;
 };
 OrientWs carve_orient(Carver& c, int32_t n, int64_t m);

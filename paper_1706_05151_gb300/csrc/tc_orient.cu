@@ -25,6 +25,7 @@ OrientWs carve_orient(Carver& c, int32_t n, int64_t) {
   OrientWs w;
   w.cursor = c.take<int32_t>(static_cast<size_t>(n > 0 ? n : 1));
   w.big_queue = c.take<int32_t>(static_cast<size_t>(n > 0 ? n : 1));
+  w.mid_queue = c.take<int32_t>(static_cast<size_t>(n > 0 ? n : 1));
   w.counters = c.take<uint32_t>(4);
   w.scan = carve_scan(c, n);
   return w;
@@ -182,7 +183,8 @@ __device__ __forceinline__ void sort_list_regs(int32_t* __restrict__ p, int len,
 // One thread per vertex.  The network size is the warp's longest short list
 // rounded up to a power of two, so one warp runs one network.
 __global__ void k_sort_small(int32_t n, const int64_t* __restrict__ offsets, int32_t* __restrict__ cols,
-                             int32_t* __restrict__ big_queue, uint32_t* __restrict__ counters, uint32_t* err) {
+                             int32_t* __restrict__ big_queue, int32_t* __restrict__ mid_queue,
+                             uint32_t* __restrict__ counters, uint32_t* err) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   // whole warps iterate together so the warp-wide reduction below is legal
   for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < n; base += stride) {
@@ -192,8 +194,10 @@ __global__ void k_sort_small(int32_t n, const int64_t* __restrict__ offsets, int
     if (v < n) {
       beg = offsets[v];
       const int64_t l = offsets[v + 1] - beg;
-      if (l > 32) {
+      if (l > kSortWarpCap) {
         big_queue[atomicAdd(&counters[0], 1u)] = static_cast<int32_t>(v);
+      } else if (l > 32) {
+        mid_queue[atomicAdd(&counters[1], 1u)] = static_cast<int32_t>(v);
       } else {
         len = static_cast<int>(l);
       }
@@ -209,7 +213,51 @@ __global__ void k_sort_small(int32_t n, const int64_t* __restrict__ offsets, int
   }
 }
 
-// One block per queued list (33 .. kSortBlockCap ids): bitonic sort in shared memory.
+// One warp per queued list of 33 .. kSortWarpCap ids: bitonic sort in shared memory.
+constexpr int kSortWarps = 8;
+__global__ void __launch_bounds__(kSortWarps * 32) k_sort_warp(const int64_t* __restrict__ offsets,
+                                                               int32_t* __restrict__ cols,
+                                                               const int32_t* __restrict__ mid_queue,
+                                                               const uint32_t* __restrict__ counters, uint32_t* err) {
+  __shared__ int32_t sbuf[kSortWarps][kSortWarpCap];
+  const int lane = lane_id(), wid = threadIdx.x >> 5;
+  int32_t* buf = sbuf[wid];
+  const uint32_t qn = counters[1];
+  for (uint32_t qi = blockIdx.x * kSortWarps + wid; qi < qn; qi += gridDim.x * kSortWarps) {
+    const int32_t v = mid_queue[qi];
+    const int64_t beg = offsets[v];
+    const int len = static_cast<int>(offsets[v + 1] - beg);  // 33 .. kSortWarpCap by construction
+    int P = 64;
+    while (P < len) P <<= 1;
+    for (int i = lane; i < P; i += 32) buf[i] = i < len ? cols[beg + i] : INT_MAX;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = lane; i < P; i += 32) {
+          const int l = i ^ j;
+          if (l > i) {
+            const bool up = (i & k) == 0;
+            const int32_t x = buf[i], y = buf[l];
+            if ((x > y) == up) {
+              buf[i] = y;
+              buf[l] = x;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    bool dup = false;
+    for (int i = lane; i < len; i += 32) {
+      cols[beg + i] = buf[i];
+      if (i > 0) dup |= buf[i] == buf[i - 1];
+    }
+    if (__any_sync(FULL, dup) && lane == 0) set_err(err, ERR_DUPLICATE);
+    __syncwarp();
+  }
+}
+
+// One block per queued list (kSortWarpCap+1 .. kSortBlockCap ids): bitonic sort in shared memory.
 __global__ void __launch_bounds__(1024) k_sort_big(const int64_t* __restrict__ offsets, int32_t* __restrict__ cols,
                                                    const int32_t* __restrict__ big_queue,
                                                    const uint32_t* __restrict__ counters, uint32_t* err) {
@@ -292,7 +340,13 @@ cudaError_t launch_orient(Ctx* ctx, int32_t n, int64_t m, const int32_t* edges, 
     const int grid_v = static_cast<int>(min64((n + 255) / 256, static_cast<int64_t>(ctx->sm_count) * 16));
     {
       Stage st(ctx, s, "orient.sort_small");
-      k_sort_small<<<grid_v, 256, 0, s>>>(n, offsets, cols, ws.big_queue, ws.counters, ctx->d_err);
+      k_sort_small<<<grid_v, 256, 0, s>>>(n, offsets, cols, ws.big_queue, ws.mid_queue, ws.counters, ctx->d_err);
+    }
+    {
+      Stage st(ctx, s, "orient.sort_mid");
+      const int grid_w = static_cast<int>(min64(static_cast<int64_t>(ctx->sm_count) * 8,
+                                                max64(1, n / (33 * kSortWarps) + 1)));
+      k_sort_warp<<<grid_w, kSortWarps * 32, 0, s>>>(offsets, cols, ws.mid_queue, ws.counters, ctx->d_err);
     }
     const size_t smem = sizeof(int32_t) * kSortBlockCap;
     if (ctx->device >= 0 && ctx->device < 64 && !g_big_attr_set[ctx->device]) {
@@ -303,9 +357,10 @@ cudaError_t launch_orient(Ctx* ctx, int32_t n, int64_t m, const int32_t* edges, 
     }
     {
       Stage st(ctx, s, "orient.sort_big");
-      k_sort_big<<<ctx->sm_count, 1024, smem, s>>>(offsets, cols, ws.big_queue, ws.counters, ctx->d_err);
+      const int grid_b = static_cast<int>(min64(ctx->sm_count, max64(1, n / (kSortWarpCap + 1) + 1)));
+      k_sort_big<<<grid_b, 1024, smem, s>>>(offsets, cols, ws.big_queue, ws.counters, ctx->d_err);
     }
-    counted(ctx, 2);
+    counted(ctx, 3);
   }
   return cudaGetLastError();
 }
