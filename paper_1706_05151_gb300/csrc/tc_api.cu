@@ -255,8 +255,8 @@ tc_status tc_workspace_size(tc_op op, int32_t n, int64_t m, size_t* bytes) {
   Carver c(nullptr);
   switch (op) {
     case TC_OP_ORIENT: tc::carve_orient(c, n, m); break;
-    case TC_OP_COUNT: tc::carve_count(c, n, false); break;
-    case TC_OP_LIST: tc::carve_count(c, n, true); break;
+    case TC_OP_COUNT: tc::carve_count(c, n, m, false); break;
+    case TC_OP_LIST: tc::carve_count(c, n, m, true); break;
     case TC_OP_SPARSIFY: tc::carve_sparsify(c, n, m); break;
     case TC_OP_BATCH: tc::carve_batch(c, n, m); break;
     default: return TC_ERR_INVALID_ARG;
@@ -293,7 +293,7 @@ static tc_status count_impl(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev,
   if ((st = check_ws(ctx, TC_OP_COUNT, g->n, g->m, ws, ws_bytes)) != TC_OK) return st;
   if ((st = begin(ctx, s)) != TC_OK) return st;
   Carver c(ws);
-  tc::CountWs w = tc::carve_count(c, g->n, false);
+  tc::CountWs w = tc::carve_count(c, g->n, g->m, false);
   cudaError_t e = cudaMemsetAsync(total_dev, 0, sizeof(uint64_t), s);
   if (e == cudaSuccess && local) e = cudaMemsetAsync(tv_dev, 0, sizeof(int64_t) * static_cast<size_t>(g->n), s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "clear outputs");
@@ -323,18 +323,15 @@ tc_status tc_list_count(tc_ctx* ctx, const tc_graph* g, int64_t* total_dev, void
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((st = begin(ctx, s)) != TC_OK) return st;
   Carver c(ws);
-  tc::CountWs w = tc::carve_count(c, g->n, true);
+  tc::CountWs w = tc::carve_count(c, g->n, g->m, true);
   cudaError_t e = cudaMemsetAsync(total_dev, 0, sizeof(int64_t), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(w.vcount, 0, sizeof(int64_t) * (static_cast<size_t>(g->n) + 1), s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "clear outputs");
   tc::CountArgs a{g->n, g->m, g->offsets, g->cols, reinterpret_cast<unsigned long long*>(total_dev), nullptr,
                   nullptr, 0};
-  e = tc::launch_count(ctx, tc::MODE_LIST_COUNT, a, w, s);
-  if (e == cudaSuccess) {
-    tc::Stage st(ctx, s, "list_count.scan");
-    e = tc::exclusive_scan_i64(w.vcount, w.voff, g->n, w.scan, s);
-    tc::counted(ctx, g->n > 0 ? 3 : 1);
-  }
+  // vertices with fewer than two out-neighbours are not visited: clear their edges' counts
+  e = cudaMemsetAsync(w.ecount, 0, sizeof(int32_t) * static_cast<size_t>(g->m), s);
+  if (e == cudaSuccess) e = tc::launch_count(ctx, tc::MODE_LIST_COUNT, a, w, s);
+  if (e == cudaSuccess) e = tc::launch_list_offsets(ctx, g->m, w, s);
   return finish(ctx, s, e);
 }
 
@@ -347,7 +344,7 @@ tc_status tc_list_write(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((st = begin(ctx, s)) != TC_OK) return st;
   Carver c(ws);
-  tc::CountWs w = tc::carve_count(c, g->n, true);
+  tc::CountWs w = tc::carve_count(c, g->n, g->m, true);
   tc::CountArgs a{g->n, g->m, g->offsets, g->cols, nullptr, nullptr, tri_dev, cap};
   return finish(ctx, s, tc::launch_count(ctx, tc::MODE_LIST_WRITE, a, w, s));
 }
@@ -361,12 +358,12 @@ tc_status tc_list(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_t cap,
   if ((st = check_ws(ctx, TC_OP_LIST, g->n, g->m, ws, ws_bytes)) != TC_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Carver c(ws);
-  tc::CountWs w = tc::carve_count(c, g->n, true);
-  // the total lands in the last entry of the offsets the count pass scans
-  int64_t* total_dev = w.voff + g->n;
+  tc::CountWs w = tc::carve_count(c, g->n, g->m, true);
+  // the total is the last entry of the edge offsets the count pass scans
+  int64_t* total_dev = w.eoff + g->m;
   const int was_async = ctx->async;
   ctx->async = 0;
-  st = tc_list_count(ctx, g, w.vcount + g->n, ws, ws_bytes, stream);
+  st = tc_list_count(ctx, g, w.eoff + g->m, ws, ws_bytes, stream);
   ctx->async = was_async;
   if (st != TC_OK) return st;
   int64_t total = 0;
@@ -390,25 +387,21 @@ tc_status tc_analyze(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, int64_
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((st = begin(ctx, s)) != TC_OK) return st;
   Carver c(ws);
-  tc::CountWs w = tc::carve_count(c, g->n, true);
+  tc::CountWs w = tc::carve_count(c, g->n, g->m, true);
   cudaError_t e = cudaMemsetAsync(total_dev, 0, sizeof(uint64_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(tv_dev, 0, sizeof(int64_t) * static_cast<size_t>(g->n), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(w.vcount, 0, sizeof(int64_t) * (static_cast<size_t>(g->n) + 1), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.ecount, 0, sizeof(int32_t) * static_cast<size_t>(g->m), s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "clear outputs");
-  // pass 1: T, T_v and the triangles of each apex vertex (into w.vcount)
+  // pass 1: T, T_v and the triangles of each oriented edge (into w.ecount)
   tc::CountArgs a{g->n, g->m, g->offsets, g->cols, reinterpret_cast<unsigned long long*>(total_dev), tv_dev,
                   nullptr, 0};
   e = tc::launch_count(ctx, tc::MODE_LOCAL, a, w, s);
   if (e == cudaSuccess && cc_dev) e = tc::launch_clustering(ctx, g->n, g->deg, tv_dev, cc_dev, s);
-  if (e == cudaSuccess) {
-    tc::Stage stg(ctx, s, "analyze.scan");
-    e = tc::exclusive_scan_i64(w.vcount, w.voff, g->n, w.scan, s);
-    tc::counted(ctx, g->n > 0 ? 3 : 1);
-  }
+  if (e == cudaSuccess) e = tc::launch_list_offsets(ctx, g->m, w, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "launch");
   // the total decides whether the triples fit: wait for it (and for the checks)
   int64_t total = 0;
-  e = cudaMemcpyAsync(&total, w.voff + g->n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  e = cudaMemcpyAsync(&total, w.eoff + g->m, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "read listing total");

@@ -17,7 +17,7 @@ BatchWs carve_batch(Carver& c, int32_t n, int64_t m) {
   w.edges = c.take<int32_t>(static_cast<size_t>(2 * (m > 0 ? m : 1)));
   w.gid = c.take<int32_t>(static_cast<size_t>(n > 0 ? n : 1));
   w.orient = carve_orient(c, n, m);
-  w.count = carve_count(c, n, false);
+  w.count = carve_count(c, n, m, false);
   return w;
 }
 

@@ -11,20 +11,27 @@
 //   k_count_tile   a warp takes 32 consecutive vertices (one coalesced load of
 //                  their offsets); their lists, contiguous in cols, are staged
 //                  as one shared-memory tile of up to kTile ids (lists longer
-//                  than kTile are queued for k_count_block).  The tile's
-//                  oriented edges (v, u) are processed 32 at a time: lane i
-//                  loads the bounds of N_u for edge i, the 32 lists N_u are laid
-//                  end to end and walked in 32-wide windows, kUnroll windows at
-//                  once so each lane has kUnroll independent global loads in
-//                  flight.  A candidate w of N_u finds its edge by a 5-step
-//                  search of the batch's prefix sums and is binary-searched in
-//                  N_v's slice of the tile.  Matches are summed per edge and per
-//                  vertex in shared memory, per warp by shuffles and per block
-//                  by one 64-bit atomicAdd.
-//   k_count_block  one block per queued vertex: N_v staged in chunks of
-//                  kBlockCap ids; the block's warps share the out-neighbour
-//                  batches (a candidate outside the chunk's id range is skipped,
-//                  so each is tested against exactly one chunk).
+//                  than tile_max are queued for k_count_block).  The tile's
+//                  oriented edges (v, u) are processed 32 at a time.  Short
+//                  lists N_u are laid end to end and walked in 32-wide windows
+//                  (an owner table maps a position to its edge), kUnroll
+//                  windows at once so each lane has kUnroll independent global
+//                  loads in flight; long lists are walked one edge at a time.
+//                  Every candidate w first meets a bitmap filter of the tile
+//                  (one shared load and a bit test); the survivors are queued
+//                  and checked exactly, 32 at a time, by binary search in N_v's
+//                  slice of the tile.
+//   k_count_block  one block per queued vertex: N_v is hashed into a shared-
+//                  memory open-addressing table (load factor at most 1/4), so
+//                  membership is exact in about one probe; the block's warps
+//                  share the out-neighbour batches.
+// Counts are summed per edge and per vertex in shared memory, per warp by
+// shuffles and per block by one 64-bit atomicAdd.
+//
+// Listing is two-pass: pass 1 records the triangles of every oriented edge,
+// a scan turns them into output offsets, and pass 2 revisits only edges that
+// have triangles, writing edge e's triangles at offset eoff[e] in candidate
+// order -- fixed positions, no atomics, the same output every run.
 #include <algorithm>
 
 #include "tc_internal.cuh"
@@ -101,16 +108,6 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x) {
   return x;
 }
 
-// ---------------------------------------------------------------------------
-// Shared batch machinery.  A batch is up to 32 oriented edges (v, u), one per
-// lane.  Short lists N_u (< kShortLen ids) are laid end to end and walked in
-// 32-wide windows (an owner table maps a position to its edge); long lists are
-// walked one edge at a time.  Every candidate w first meets a bitmap filter of
-// the staged lists (one shared load and a bit test); the few that pass (true
-// matches and about S / 2^bits false positives) are queued and checked exactly,
-// 32 at a time, by binary search in the staged N_v.
-// ---------------------------------------------------------------------------
-
 // Multiplicative hash of (salt, id) onto a 2^LOG2-bit filter.
 template <int LOG2>
 __device__ __forceinline__ uint32_t fbit(int32_t w, int32_t salt) {
@@ -129,92 +126,108 @@ __device__ __forceinline__ void fset(uint32_t* bits, int32_t w, int32_t salt) {
   atomicOr(&bits[h >> 5], 1u << (h & 31));
 }
 
+// Per-warp state of one batch of up to 32 oriented edges (v, u), one per lane.
 struct BatchSmem {
   int64_t beg[32];        // short list: start of N_u minus its flattened offset; long list: start of N_u
+  int64_t eg[32];         // global index of the edge (its position in cols)
   int32_t u[32];
   int32_t lo[32];         // tile kernel: N_v's slice [lo, lo + len) of the tile
   int32_t len[32];
-  int32_t salt[32];       // filter salt: chunk lane of v (tile kernel), 0 (block kernel)
+  int32_t salt[32];       // tile kernel: filter salt (chunk lane of v)
   uint32_t cnt[32];       // matches of the edge
+  uint32_t erun[32];      // listing: triples of the edge written so far
   int32_t qw[64];         // filter survivors: candidate id ...
   int32_t qs[64];         // ... and its edge
   uint8_t own[kOwnCap];   // flattened position -> edge, short lists
 };
 
-struct Probe {            // what the candidates are tested against
-  const int32_t* sv;      // tile kernel: the tile; block kernel: the staged chunk of N_v
-  const uint32_t* bits;   // filter of sv
-  int top;                // binary-search span (power of two)
-  int len;                // block kernel: chunk length
-  int32_t lo, hi;         // block kernel: id range of the chunk
-};
-
-template <bool TILE>
-__device__ __forceinline__ bool passes(const Probe& pr, int32_t salt, int32_t w) {
-  return ftest<kTileBitsLog2>(pr.bits, w, salt);
+// Fills the batch record for this lane's edge; *tot is the flattened length of
+// the short lists, *is_short whether this lane's list is one of them, *len its length.
+__device__ __forceinline__ void batch_setup(BatchSmem& bs, const CountArgs& a, const CountWs& ws, int32_t u,
+                                            bool act, int64_t eg, int32_t salt, int32_t lo, int32_t vlen,
+                                            int& tot, bool& is_short, int32_t& len, uint32_t* err, bool list_write) {
+  const int lane = lane_id();
+  int64_t ub = 0;
+  len = 0;
+  // the listing write pass walks only edges that have triangles
+  if (act && (!list_write || ws.ecount[eg] > 0)) len = list_bounds(a, u, ub, err);
+  is_short = len < kShortLen;
+  const int32_t slen = is_short ? len : 0;
+  const int32_t incl = warp_incl_scan(slen);
+  tot = __shfl_sync(FULL, incl, 31);
+  const int32_t excl = incl - slen;
+  __syncwarp();
+  bs.beg[lane] = is_short ? ub - excl : ub;
+  bs.eg[lane] = eg;
+  bs.u[lane] = u;
+  bs.lo[lane] = lo;
+  bs.len[lane] = vlen;
+  bs.salt[lane] = salt;
+  bs.cnt[lane] = 0;
+  bs.erun[lane] = 0;
+  for (int i = 0; i < slen; ++i) bs.own[excl + i] = static_cast<uint8_t>(lane);
+  __syncwarp();
 }
 
+// Listing: write this lane's triple (if f) at its edge's offset plus the
+// edge's running count; lanes of one edge are contiguous and in candidate order.
+__device__ __forceinline__ void write_triples(BatchSmem& bs, bool has, bool f, int s, int32_t v, int32_t w,
+                                             const CountArgs& a, const CountWs& ws, uint32_t* err) {
+  const int lane = lane_id();
+  const unsigned fm = __ballot_sync(FULL, f);
+  if (!fm) return;
+  const unsigned same = __match_any_sync(FULL, has ? s : 32 + lane);
+  if (f) {
+    const int64_t idx = ws.eoff[bs.eg[s]] + bs.erun[s] + __popc(fm & same & lanemask_lt());
+    if (idx < a.cap) {
+      a.tri[3 * idx] = v;
+      a.tri[3 * idx + 1] = bs.u[s];
+      a.tri[3 * idx + 2] = w;
+    } else {
+      set_err(err, ERR_CAPACITY);
+    }
+  }
+  __syncwarp();
+  if (has && lane == 31 - __clz(same)) bs.erun[s] += __popc(fm & same);
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Tile kernel
+// ---------------------------------------------------------------------------
+
+struct TileSmem {
+  int32_t tile[kTile];
+  uint32_t bits[(1 << kTileBitsLog2) / 32];
+  int32_t vlo[32];     // tile start of each chunk lane's list (-1 before the group, > S after)
+  uint32_t vcnt[32];   // triangles with apex v (chunk lane)
+  BatchSmem bs;
+};
+
 // Exact check of the first `cnt` queued survivors, with the per-mode effects.
-template <int MODE, bool TILE>
-__device__ __forceinline__ void exact_flush(BatchSmem& bs, const Probe& pr, int cnt, int32_t vbase_or_v, int32_t* vrun,
-                                            unsigned long long* cursor, const CountArgs& a, const CountWs& ws,
-                                            uint32_t* err) {
+template <int MODE>
+__device__ __forceinline__ void exact_flush(TileSmem& sm, int cnt, int top, int32_t vbase, const CountArgs& a,
+                                            const CountWs& ws, uint32_t* err) {
+  BatchSmem& bs = sm.bs;
   const int lane = lane_id();
   __syncwarp();
   const bool has = lane < cnt;
   const int s = has ? bs.qs[lane] : 0;
   const int32_t w = has ? bs.qw[lane] : 0;
-  bool f = false;
-  if (has) f = TILE ? member(pr.sv + bs.lo[s], bs.len[s], pr.top, w) : member(pr.sv, pr.len, pr.top, w);
+  const bool f = has && member(sm.tile + bs.lo[s], bs.len[s], top, w);
   if (f) {
     atomicAdd(&bs.cnt[s], 1u);
     if (MODE == MODE_LOCAL) atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + w), 1ull);
   }
-  if (MODE == MODE_LIST_WRITE) {
-    const unsigned fm = __ballot_sync(FULL, f);
-    if (fm) {
-      if (TILE) {
-        // triples of one apex vertex are written in queue order at voff[v] + running count
-        const int vl = bs.salt[s];
-        const unsigned same = __match_any_sync(FULL, has ? vl : 32 + lane);
-        if (f) {
-          const int32_t v = vbase_or_v + vl;
-          const int64_t idx = ws.voff[v] + vrun[vl] + __popc(fm & same & lanemask_lt());
-          if (idx < a.cap) {
-            a.tri[3 * idx] = v;
-            a.tri[3 * idx + 1] = bs.u[s];
-            a.tri[3 * idx + 2] = w;
-          } else {
-            set_err(err, ERR_CAPACITY);
-          }
-        }
-        __syncwarp();
-        if (has && lane == 31 - __clz(same)) vrun[vl] += __popc(fm & same);
-      } else {
-        unsigned long long b0 = 0;
-        if (lane == 0) b0 = atomicAdd(cursor, static_cast<unsigned long long>(__popc(fm)));
-        const int64_t base = static_cast<int64_t>(__shfl_sync(FULL, b0, 0));
-        if (f) {
-          const int64_t idx = base + __popc(fm & lanemask_lt());
-          if (idx < a.cap) {
-            a.tri[3 * idx] = vbase_or_v;
-            a.tri[3 * idx + 1] = bs.u[s];
-            a.tri[3 * idx + 2] = w;
-          } else {
-            set_err(err, ERR_CAPACITY);
-          }
-        }
-      }
-    }
-  }
+  if (MODE == MODE_LIST_WRITE) write_triples(bs, has, f, s, vbase + bs.salt[s], w, a, ws, err);
   __syncwarp();
 }
 
 // Queue this window's survivors; check 32 of them once 32 are waiting.
-template <int MODE, bool TILE>
-__device__ __forceinline__ void push(BatchSmem& bs, const Probe& pr, bool pass, int32_t w, int s, int& qn,
-                                     int32_t vbase_or_v, int32_t* vrun, unsigned long long* cursor,
+template <int MODE>
+__device__ __forceinline__ void push(TileSmem& sm, bool pass, int32_t w, int s, int& qn, int top, int32_t vbase,
                                      const CountArgs& a, const CountWs& ws, uint32_t* err) {
+  BatchSmem& bs = sm.bs;
   const int lane = lane_id();
   const unsigned m = __ballot_sync(FULL, pass);
   if (!m) return;
@@ -225,7 +238,7 @@ __device__ __forceinline__ void push(BatchSmem& bs, const Probe& pr, bool pass, 
   }
   qn += __popc(m);
   if (qn >= 32) {
-    exact_flush<MODE, TILE>(bs, pr, 32, vbase_or_v, vrun, cursor, a, ws, err);
+    exact_flush<MODE>(sm, 32, top, vbase, a, ws, err);
     const int rest = qn - 32;
     int32_t tw = 0, ts = 0;
     if (lane < rest) {
@@ -242,33 +255,18 @@ __device__ __forceinline__ void push(BatchSmem& bs, const Probe& pr, bool pass, 
   }
 }
 
-// One batch of edges (v, u): u on this lane if `act`.  Returns the matches of
-// this lane's edge.  salt/lo/vlen describe this lane's N_v (tile kernel).
-template <int MODE, bool TILE>
-__device__ __forceinline__ uint32_t process_batch(BatchSmem& bs, const Probe& pr, int32_t u, bool act, int32_t salt,
-                                                  int32_t lo, int32_t vlen, int32_t vbase_or_v, int32_t* vrun,
-                                                  unsigned long long* cursor, const CountArgs& a,
-                                                  const CountWs& ws, uint32_t* err) {
+// One batch of the tile's edges; returns the matches of this lane's edge.
+template <int MODE>
+__device__ __forceinline__ uint32_t tile_batch(TileSmem& sm, int top, int32_t u, bool act, int64_t eg, int32_t vl,
+                                               int32_t lo, int32_t vlen, int32_t vbase, const CountArgs& a,
+                                               const CountWs& ws, uint32_t* err) {
+  BatchSmem& bs = sm.bs;
   const int lane = lane_id();
-  int64_t ub = 0;
-  int32_t len = 0;
-  if (act) len = list_bounds(a, u, ub, err);
-  const bool is_short = len < kShortLen;
-  const int32_t slen = is_short ? len : 0;
-  const int32_t incl = warp_incl_scan(slen);
-  const int32_t tot = __shfl_sync(FULL, incl, 31);
-  const int32_t excl = incl - slen;
-  __syncwarp();
-  bs.beg[lane] = is_short ? ub - excl : ub;
-  bs.u[lane] = u;
-  bs.lo[lane] = lo;
-  bs.len[lane] = vlen;
-  bs.salt[lane] = salt;
-  bs.cnt[lane] = 0;
-  for (int i = 0; i < slen; ++i) bs.own[excl + i] = static_cast<uint8_t>(lane);
-  __syncwarp();
+  int tot;
+  bool is_short;
+  int32_t len;
+  batch_setup(bs, a, ws, u, act, eg, vl, lo, vlen, tot, is_short, len, err, MODE == MODE_LIST_WRITE);
   int qn = 0;
-  // short lists, end to end
   for (int32_t p0 = 0; p0 < tot; p0 += 32 * kUnroll) {
     int32_t w[kUnroll];
     int s[kUnroll];
@@ -285,12 +283,11 @@ __device__ __forceinline__ uint32_t process_batch(BatchSmem& bs, const Probe& pr
 #pragma unroll
     for (int k = 0; k < kUnroll; ++k) {
       const int32_t p = p0 + 32 * k + lane;
-      const bool pass = p < tot && passes<TILE>(pr, bs.salt[s[k]], w[k]);
-      push<MODE, TILE>(bs, pr, pass, w[k], s[k], qn, vbase_or_v, vrun, cursor, a, ws, err);
+      const bool pass = p < tot && ftest<kTileBitsLog2>(sm.bits, w[k], bs.salt[s[k]]);
+      push<MODE>(sm, pass, w[k], s[k], qn, top, vbase, a, ws, err);
     }
   }
-  // long lists, one edge at a time
-  unsigned lm = __ballot_sync(FULL, act && !is_short);
+  unsigned lm = __ballot_sync(FULL, len > 0 && !is_short);
   while (lm) {
     const int e = __ffs(lm) - 1;
     lm &= lm - 1;
@@ -307,19 +304,15 @@ __device__ __forceinline__ uint32_t process_batch(BatchSmem& bs, const Probe& pr
 #pragma unroll
       for (int k = 0; k < kUnroll; ++k) {
         const int32_t p = p0 + 32 * k + lane;
-        const bool pass = p < le && passes<TILE>(pr, se, w[k]);
-        push<MODE, TILE>(bs, pr, pass, w[k], e, qn, vbase_or_v, vrun, cursor, a, ws, err);
+        const bool pass = p < le && ftest<kTileBitsLog2>(sm.bits, w[k], se);
+        push<MODE>(sm, pass, w[k], e, qn, top, vbase, a, ws, err);
       }
     }
   }
-  if (qn) exact_flush<MODE, TILE>(bs, pr, qn, vbase_or_v, vrun, cursor, a, ws, err);
+  if (qn) exact_flush<MODE>(sm, qn, top, vbase, a, ws, err);
   __syncwarp();
   return act ? bs.cnt[lane] : 0u;
 }
-
-// ---------------------------------------------------------------------------
-// Tile kernel
-// ---------------------------------------------------------------------------
 
 // Batched form: add each apex vertex's count to its graph's total.  Graph ids
 // of consecutive vertices form runs; one lane per run adds the run's sum.
@@ -337,15 +330,6 @@ __device__ __forceinline__ void add_graph_totals(const CountArgs& a, bool in_gro
   const uint32_t sum = at_end - (lane > 0 ? before : 0u);
   if (head && in_group && sum) atomicAdd(a.graph_total + key, static_cast<unsigned long long>(sum));
 }
-
-struct TileSmem {
-  int32_t tile[kTile];
-  uint32_t bits[(1 << kTileBitsLog2) / 32];
-  int32_t vlo[32];     // tile start of each chunk lane's list (-1 before the group, > S after)
-  uint32_t vcnt[32];   // triangles with apex v (chunk lane)
-  int32_t vrun[32];    // listing: triples written so far per chunk lane
-  BatchSmem bs;
-};
 
 template <int MODE>
 __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, CountWs ws, uint32_t* err) {
@@ -372,7 +356,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, Cou
     }
     const int64_t d = e - b;
     // the listing write pass only revisits apex vertices that have triangles
-    const bool skip = MODE == MODE_LIST_WRITE && valid && ws.vcount[v] == 0;
+    const bool skip = MODE == MODE_LIST_WRITE && valid && ws.eoff[e] == ws.eoff[b];
     const bool big = valid && !skip && d > a.tile_max;
     const unsigned bigmask = __ballot_sync(FULL, big);
     if (bigmask) {
@@ -409,7 +393,6 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, Cou
       const int32_t lo = incl - len;
       sm.vlo[lane] = lane < g0 ? -1 : (lane < g1 ? lo : S + 1);
       sm.vcnt[lane] = 0;
-      sm.vrun[lane] = 0;
       if (__any_sync(FULL, bad)) {
         if (lane == 0) set_err(err, ERR_BAD_ID);
         g0 = g1;
@@ -418,7 +401,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, Cou
       __syncwarp();
       for (int i = 0; i < glen; ++i) fset<kTileBitsLog2>(sm.bits, sm.tile[lo + i], lane);
       const int maxlen = __reduce_max_sync(FULL, glen);
-      const Probe pr{sm.tile, sm.bits, maxlen > 0 ? 1 << (31 - __clz(maxlen)) : 0, 0, 0, 0};
+      const int top = maxlen > 0 ? 1 << (31 - __clz(maxlen)) : 0;
       __syncwarp();
       for (int t0 = 0; t0 < S; t0 += 32) {
         const int t = t0 + lane;
@@ -426,8 +409,10 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, Cou
         const int vl = act ? search32(sm.vlo, static_cast<int32_t>(t)) : 0;
         const int32_t u = act ? sm.tile[t] : 0;
         const int32_t vlen = __shfl_sync(FULL, glen, vl);
-        const uint32_t c = process_batch<MODE, true>(sm.bs, pr, u, act, vl, sm.vlo[vl], vlen,
-                                                     static_cast<int32_t>(base), sm.vrun, nullptr, a, ws, err);
+        const uint32_t c = tile_batch<MODE>(sm, top, u, act, start + t, vl, sm.vlo[vl], vlen,
+                                            static_cast<int32_t>(base), a, ws, err);
+        if (act && (MODE == MODE_LOCAL || MODE == MODE_LIST_COUNT) && ws.ecount)
+          ws.ecount[start + t] = static_cast<int32_t>(c);
         if (c) {
           if (MODE == MODE_LOCAL)
             atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + u), static_cast<unsigned long long>(c));
@@ -439,7 +424,6 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, Cou
       if (in_group) {
         if (MODE == MODE_LOCAL && cv)
           atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + v), static_cast<unsigned long long>(cv));
-        if ((MODE == MODE_LIST_COUNT || MODE == MODE_LOCAL) && ws.vcount) ws.vcount[v] = cv;
         acc += cv;
       }
       if (MODE != MODE_LIST_WRITE && a.graph_total) add_graph_totals(a, in_group, v, cv);
@@ -461,92 +445,71 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, Cou
 // Block kernel (lists longer than tile_max).  Heavy apex vertices get a whole
 // block; N_v is hashed into a shared-memory open-addressing table (load factor
 // at most 1/4) so that membership is exact in about one probe, with no filter,
-// no survivor queue and no binary search.
+// no survivor queue and no binary search.  For per-vertex counts each slot
+// also counts its matches, so T_w is added once per (v, w) instead of once
+// per triangle (the w of a skewed graph are hubs: one global counter each).
 // ---------------------------------------------------------------------------
 
-constexpr int kHashSlotsLog2 = 13;                   // 8192 slots (32 KB)
-constexpr int kHashCap = (1 << kHashSlotsLog2) / 4;  // ids of N_v per pass
-
-__device__ __forceinline__ uint32_t slot_of(int32_t w) {
-  return (static_cast<uint32_t>(w) * 0x9E3779B1u) >> (32 - kHashSlotsLog2);
-}
-
-__device__ __forceinline__ bool hash_member(const int32_t* tab, int32_t w) {
-  if (w < 0) return false;
-  uint32_t h = slot_of(w);
-  for (int probe = 0; probe < (1 << kHashSlotsLog2); ++probe) {  // bounded: the table is never full
-    const int32_t x = tab[h];
-    if (x == w) return true;
-    if (x < 0) return false;
-    h = (h + 1) & ((1u << kHashSlotsLog2) - 1);
-  }
-  return false;
-}
-
-__device__ __forceinline__ void hash_insert(int32_t* tab, int32_t w) {
-  uint32_t h = slot_of(w);
-  for (int probe = 0; probe < (1 << kHashSlotsLog2); ++probe) {
-    const int32_t prev = atomicCAS(&tab[h], -1, w);
-    if (prev == -1 || prev == w) return;
-    h = (h + 1) & ((1u << kHashSlotsLog2) - 1);
-  }
-}
-
-struct HashBatch {
-  int64_t beg[32];        // short list: start of N_u minus its flattened offset; long list: start of N_u
-  int32_t u[32];
-  uint32_t cnt[32];       // matches of the edge
-  uint8_t own[kOwnCap];   // flattened position -> edge, short lists
+template <int MODE>
+struct HashCfg {
+  static constexpr int kLog2 = MODE == MODE_LOCAL ? 12 : 13;   // slots (keys, plus counts when LOCAL)
+  static constexpr int kSlots = 1 << kLog2;
+  static constexpr int kCap = kSlots / 4;                        // ids of N_v per pass
+  static constexpr size_t kBytes = sizeof(int32_t) * kSlots * (MODE == MODE_LOCAL ? 2 : 1);
 };
 
+template <int LOG2>
+__device__ __forceinline__ uint32_t slot_of(int32_t w) {
+  return (static_cast<uint32_t>(w) * 0x9E3779B1u) >> (32 - LOG2);
+}
+
+// Slot of w in the table, or -1.
+template <int LOG2>
+__device__ __forceinline__ int hash_find(const int32_t* tab, int32_t w) {
+  if (w < 0) return -1;
+  uint32_t h = slot_of<LOG2>(w);
+  for (int probe = 0; probe < (1 << LOG2); ++probe) {  // bounded: the table is never full
+    const int32_t x = tab[h];
+    if (x == w) return static_cast<int>(h);
+    if (x < 0) return -1;
+    h = (h + 1) & ((1u << LOG2) - 1);
+  }
+  return -1;
+}
+
+template <int LOG2>
+__device__ __forceinline__ void hash_insert(int32_t* tab, int32_t w) {
+  uint32_t h = slot_of<LOG2>(w);
+  for (int probe = 0; probe < (1 << LOG2); ++probe) {
+    const int32_t prev = atomicCAS(&tab[h], -1, w);
+    if (prev == -1 || prev == w) return;
+    h = (h + 1) & ((1u << LOG2) - 1);
+  }
+}
+
 template <int MODE>
-__device__ __forceinline__ void hash_record(HashBatch& hb, bool found, int32_t w, int s, int32_t v,
-                                            unsigned long long* cursor, const CountArgs& a, uint32_t* err) {
+__device__ __forceinline__ void hash_record(BatchSmem& bs, uint32_t* slot_cnt, bool has, int slot, int32_t w, int s,
+                                            int32_t v, const CountArgs& a, const CountWs& ws, uint32_t* err) {
+  const bool found = slot >= 0;
   if (found) {
-    atomicAdd(&hb.cnt[s], 1u);
-    if (MODE == MODE_LOCAL) atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + w), 1ull);
+    atomicAdd(&bs.cnt[s], 1u);
+    if (MODE == MODE_LOCAL) atomicAdd(&slot_cnt[slot], 1u);
   }
-  if (MODE == MODE_LIST_WRITE) {
-    const unsigned fm = __ballot_sync(FULL, found);
-    if (fm) {
-      unsigned long long b0 = 0;
-      if (lane_id() == 0) b0 = atomicAdd(cursor, static_cast<unsigned long long>(__popc(fm)));
-      const int64_t base = static_cast<int64_t>(__shfl_sync(FULL, b0, 0));
-      if (found) {
-        const int64_t idx = base + __popc(fm & lanemask_lt());
-        if (idx < a.cap) {
-          a.tri[3 * idx] = v;
-          a.tri[3 * idx + 1] = hb.u[s];
-          a.tri[3 * idx + 2] = w;
-        } else {
-          set_err(err, ERR_CAPACITY);
-        }
-      }
-    }
-  }
+  if (MODE == MODE_LIST_WRITE) write_triples(bs, has, found, s, v, w, a, ws, err);
 }
 
 // One batch of edges (v, u), u on this lane if `act`, against the hashed chunk
 // of N_v whose ids lie in [lo, hi].  Returns the matches of this lane's edge.
 template <int MODE>
-__device__ __forceinline__ uint32_t hash_batch(HashBatch& hb, const int32_t* tab, int32_t lo, int32_t hi, int32_t u,
-                                               bool act, int32_t v, unsigned long long* cursor, const CountArgs& a,
-                                               uint32_t* err) {
+__device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab, uint32_t* slot_cnt, int32_t lo,
+                                               int32_t hi, int32_t u, bool act, int64_t eg, int32_t v,
+                                               const CountArgs& a, const CountWs& ws, uint32_t* err) {
+  constexpr int L = HashCfg<MODE>::kLog2;
   const int lane = lane_id();
-  int64_t ub = 0;
-  int32_t len = 0;
-  if (act) len = list_bounds(a, u, ub, err);
-  const bool is_short = len < kShortLen;
-  const int32_t slen = is_short ? len : 0;
-  const int32_t incl = warp_incl_scan(slen);
-  const int32_t tot = __shfl_sync(FULL, incl, 31);
-  const int32_t excl = incl - slen;
-  __syncwarp();
-  hb.beg[lane] = is_short ? ub - excl : ub;
-  hb.u[lane] = u;
-  hb.cnt[lane] = 0;
-  for (int i = 0; i < slen; ++i) hb.own[excl + i] = static_cast<uint8_t>(lane);
-  __syncwarp();
+  int tot;
+  bool is_short;
+  int32_t len;
+  batch_setup(bs, a, ws, u, act, eg, 0, 0, 0, tot, is_short, len, err, MODE == MODE_LIST_WRITE);
   for (int32_t p0 = 0; p0 < tot; p0 += 32 * kUnroll) {
     int32_t w[kUnroll];
     int s[kUnroll];
@@ -556,21 +519,22 @@ __device__ __forceinline__ uint32_t hash_batch(HashBatch& hb, const int32_t* tab
       s[k] = 0;
       w[k] = -1;
       if (p < tot) {
-        s[k] = hb.own[p];
-        w[k] = a.cols[hb.beg[s[k]] + p];
+        s[k] = bs.own[p];
+        w[k] = a.cols[bs.beg[s[k]] + p];
       }
     }
 #pragma unroll
     for (int k = 0; k < kUnroll; ++k) {
-      const bool found = w[k] >= lo && w[k] <= hi && hash_member(tab, w[k]);
-      hash_record<MODE>(hb, found, w[k], s[k], v, cursor, a, err);
+      const int32_t p = p0 + 32 * k + lane;
+      const int slot = (w[k] >= lo && w[k] <= hi) ? hash_find<L>(tab, w[k]) : -1;
+      hash_record<MODE>(bs, slot_cnt, p < tot, slot, w[k], s[k], v, a, ws, err);
     }
   }
-  unsigned lm = __ballot_sync(FULL, act && !is_short);
+  unsigned lm = __ballot_sync(FULL, len > 0 && !is_short);
   while (lm) {
     const int e = __ffs(lm) - 1;
     lm &= lm - 1;
-    const int64_t b = hb.beg[e];
+    const int64_t b = bs.beg[e];
     const int32_t le = __shfl_sync(FULL, len, e);
     for (int32_t p0 = 0; p0 < le; p0 += 32 * kUnroll) {
       int32_t w[kUnroll];
@@ -581,21 +545,23 @@ __device__ __forceinline__ uint32_t hash_batch(HashBatch& hb, const int32_t* tab
       }
 #pragma unroll
       for (int k = 0; k < kUnroll; ++k) {
-        const bool found = w[k] >= lo && w[k] <= hi && hash_member(tab, w[k]);
-        hash_record<MODE>(hb, found, w[k], e, v, cursor, a, err);
+        const int32_t p = p0 + 32 * k + lane;
+        const int slot = (w[k] >= lo && w[k] <= hi) ? hash_find<L>(tab, w[k]) : -1;
+        hash_record<MODE>(bs, slot_cnt, p < le, slot, w[k], e, v, a, ws, err);
       }
     }
   }
   __syncwarp();
-  return act ? hb.cnt[lane] : 0u;
+  return act ? bs.cnt[lane] : 0u;
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a, CountWs ws, uint32_t* err) {
+  using H = HashCfg<MODE>;
   extern __shared__ int32_t tab[];
-  __shared__ HashBatch s_hb[kBlockWarps];
+  uint32_t* slot_cnt = reinterpret_cast<uint32_t*>(tab + H::kSlots);  // LOCAL only
+  __shared__ BatchSmem s_b[kBlockWarps];
   __shared__ unsigned long long s_red[kBlockWarps];
-  __shared__ unsigned long long s_cursor;
   const int lane = lane_id(), wid = threadIdx.x >> 5;
   unsigned long long acc = 0;
   const uint32_t qn = ws.counters[0];
@@ -603,18 +569,20 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
     const int32_t v = ws.big_queue[qi];
     const int64_t b = a.offsets[v], e = a.offsets[v + 1];
     const int64_t dv = e - b;
-    if (threadIdx.x == 0 && MODE == MODE_LIST_WRITE) s_cursor = static_cast<unsigned long long>(ws.voff[v]);
     unsigned long long cv = 0;
-    for (int64_t c0 = 0; c0 < dv; c0 += kHashCap) {
-      const int clen = static_cast<int>(min64(kHashCap, dv - c0));
+    for (int64_t c0 = 0; c0 < dv; c0 += H::kCap) {
+      const int clen = static_cast<int>(min64(H::kCap, dv - c0));
       __syncthreads();
-      for (int i = threadIdx.x; i < (1 << kHashSlotsLog2); i += blockDim.x) tab[i] = -1;
+      for (int i = threadIdx.x; i < H::kSlots; i += blockDim.x) {
+        tab[i] = -1;
+        if (MODE == MODE_LOCAL) slot_cnt[i] = 0;
+      }
       __syncthreads();
       bool bad = false;
       for (int i = threadIdx.x; i < clen; i += blockDim.x) {
         const int32_t x = a.cols[b + c0 + i];
         if (static_cast<uint32_t>(x) >= static_cast<uint32_t>(a.n)) bad = true;
-        else hash_insert(tab, x);
+        else hash_insert<H::kLog2>(tab, x);
       }
       if (__syncthreads_or(bad)) {
         if (threadIdx.x == 0) set_err(err, ERR_BAD_ID);
@@ -626,10 +594,22 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
         const int nb = static_cast<int>(min64(32, dv - ub));
         const bool act = lane < nb;
         const int32_t u = act ? a.cols[b + ub + lane] : 0;
-        const uint32_t c = hash_batch<MODE>(s_hb[wid], tab, lo, hi, u, act, v, &s_cursor, a, err);
+        const uint32_t c = hash_batch<MODE>(s_b[wid], tab, slot_cnt, lo, hi, u, act, b + ub + lane, v, a, ws, err);
         cv += c;
+        if (act && (MODE == MODE_LOCAL || MODE == MODE_LIST_COUNT) && ws.ecount) {
+          // the same lane holds the same edge in every chunk
+          if (c0 == 0) ws.ecount[b + ub + lane] = static_cast<int32_t>(c);
+          else ws.ecount[b + ub + lane] += static_cast<int32_t>(c);
+        }
         if (MODE == MODE_LOCAL && c)
           atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + u), static_cast<unsigned long long>(c));
+      }
+      if (MODE == MODE_LOCAL) {  // T_w once per (v, w) of this chunk
+        __syncthreads();
+        for (int i = threadIdx.x; i < H::kSlots; i += blockDim.x)
+          if (slot_cnt[i])
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + tab[i]),
+                      static_cast<unsigned long long>(slot_cnt[i]));
       }
     }
     cv = warp_sum64(cv);
@@ -639,7 +619,6 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
       unsigned long long t = 0;
       for (int w = 0; w < kBlockWarps; ++w) t += s_red[w];
       if (MODE == MODE_LOCAL && t) atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + v), t);
-      if ((MODE == MODE_LIST_COUNT || MODE == MODE_LOCAL) && ws.vcount) ws.vcount[v] = static_cast<int64_t>(t);
       if (MODE != MODE_LIST_WRITE && a.graph_total && t) atomicAdd(a.graph_total + a.gid[v], t);
       acc += t;
     }
@@ -674,7 +653,7 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
     Stage st(ctx, s, kNames[MODE][0]);
     k_count_tile<MODE><<<tgrid, kTileWarps * 32, 0, s>>>(a, ws, ctx->d_err);
   }
-  const size_t smem = sizeof(int32_t) << kHashSlotsLog2;
+  const size_t smem = HashCfg<MODE>::kBytes;
   const int bgrid = static_cast<int>(min64(
       persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_block<MODE>), kBlockWarps * 32, smem),
       max64(1, a.m / (a.tile_max + 1))));  // at most m / (tile_max + 1) lists go to this kernel
@@ -688,14 +667,14 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
 
 }  // namespace
 
-CountWs carve_count(Carver& c, int32_t n, bool listing) {
+CountWs carve_count(Carver& c, int32_t n, int64_t m, bool listing) {
   CountWs w{};
   w.big_queue = c.take<int32_t>(static_cast<size_t>(n > 0 ? n : 1));
   w.counters = c.take<uint32_t>(4);
   if (listing) {
-    w.vcount = c.take<int64_t>(static_cast<size_t>(n) + 1);
-    w.voff = c.take<int64_t>(static_cast<size_t>(n) + 1);
-    w.scan = carve_scan(c, n);
+    w.ecount = c.take<int32_t>(static_cast<size_t>(m > 0 ? m : 1));
+    w.eoff = c.take<int64_t>(static_cast<size_t>(m) + 1);
+    w.scan = carve_scan(c, m);
   }
   return w;
 }
@@ -722,6 +701,12 @@ cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a_in, CountW
     case MODE_LIST_WRITE: return launch_mode<MODE_LIST_WRITE>(ctx, a, ws, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_list_offsets(Ctx* ctx, int64_t m, CountWs ws, cudaStream_t s) {
+  Stage st(ctx, s, "list.scan");
+  counted(ctx, m > 0 ? 3 : 1);
+  return exclusive_scan_i32(ws.ecount, ws.eoff, m, ws.scan, s);
 }
 
 cudaError_t launch_clustering(Ctx* ctx, int32_t n, const int32_t* deg, const int64_t* tv, double* cc,

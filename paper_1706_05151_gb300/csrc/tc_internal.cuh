@@ -103,12 +103,12 @@ inline ScanWs carve_scan(Carver& c, int64_t n) { return ScanWs{c.take<int64_t>(s
 
 struct CountWs {
   int32_t* big_queue;   // vertices left to the block kernel
-  uint32_t* counters;   // [0] queue length, [1] vertex cursor of the warp kernel, [2..3] spare
-  int64_t* vcount;      // listing: triangles per apex vertex (n)
-  int64_t* voff;        // listing: output offsets (n + 1)
-  ScanWs scan;
+  uint32_t* counters;   // [0] queue length, [1] vertex cursor of the tile kernel, [2..3] spare
+  int32_t* ecount;      // listing: triangles per oriented edge (m)
+  int64_t* eoff;        // listing: output offset per oriented edge (m + 1; eoff[m] = T)
+  ScanWs scan;          // listing: scan over the m edge counts
 };
-CountWs carve_count(Carver& c, int32_t n, bool listing);
+CountWs carve_count(Carver& c, int32_t n, int64_t m, bool listing);
 
 struct OrientWs {
   int32_t* cursor;      // fill cursor per vertex
@@ -163,6 +163,8 @@ struct CountArgs {
   int32_t tile_max = 0;                       // lists longer than this go to the block kernel (set by launch_count)
 };
 cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a, CountWs ws, cudaStream_t s);
+// Listing: eoff = exclusive scan of ecount (after a MODE_LIST_COUNT or MODE_LOCAL pass).
+cudaError_t launch_list_offsets(Ctx* ctx, int64_t m, CountWs ws, cudaStream_t s);
 cudaError_t launch_clustering(Ctx* ctx, int32_t n, const int32_t* deg, const int64_t* tv, double* cc, cudaStream_t s);
 
 cudaError_t launch_sparsify(Ctx* ctx, int32_t n, int64_t m, const int64_t* offsets, const int32_t* cols,

@@ -204,7 +204,7 @@ cudaError_t launch_request(tc_server* s, Request& r, GraphRec& g) {
   cudaError_t e = cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), st);
   tc::Carver c(r.ws);
   if (r.kind == TC_REQ_COUNT || r.kind == TC_REQ_LOCAL) {
-    tc::CountWs w = tc::carve_count(c, g.n, false);
+    tc::CountWs w = tc::carve_count(c, g.n, g.m, false);
     int64_t* tv = r.kind == TC_REQ_LOCAL ? reinterpret_cast<int64_t*>(static_cast<char*>(r.out) + 256) : nullptr;
     double* cc = r.kind == TC_REQ_LOCAL ? reinterpret_cast<double*>(tv + g.n) : nullptr;
     if (e == cudaSuccess) e = cudaMemsetAsync(total, 0, sizeof(uint64_t), st);
@@ -214,15 +214,14 @@ cudaError_t launch_request(tc_server* s, Request& r, GraphRec& g) {
     if (e == cudaSuccess && cc) e = tc::launch_clustering(ctx, g.n, g.deg, tv, cc, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_total, total, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
   } else {
-    tc::CountWs w = tc::carve_count(c, g.n, true);
+    tc::CountWs w = tc::carve_count(c, g.n, g.m, true);
     if (r.phase == 0) {
-      if (e == cudaSuccess) e = cudaMemsetAsync(w.vcount, 0, sizeof(int64_t) * (static_cast<size_t>(g.n) + 1), st);
-      tc::CountArgs a{g.n, g.m, g.offsets, g.cols, reinterpret_cast<unsigned long long*>(w.vcount + g.n), nullptr,
-                      nullptr, 0};
+      if (e == cudaSuccess) e = cudaMemsetAsync(w.ecount, 0, sizeof(int32_t) * static_cast<size_t>(g.m), st);
+      tc::CountArgs a{g.n, g.m, g.offsets, g.cols, nullptr, nullptr, nullptr, 0};
       if (e == cudaSuccess) e = tc::launch_count(ctx, tc::MODE_LIST_COUNT, a, w, st);
-      if (e == cudaSuccess) e = tc::exclusive_scan_i64(w.vcount, w.voff, g.n, w.scan, st);
+      if (e == cudaSuccess) e = tc::launch_list_offsets(ctx, g.m, w, st);
       if (e == cudaSuccess)
-        e = cudaMemcpyAsync(sl.h_total, w.voff + g.n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(sl.h_total, w.eoff + g.m, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
     } else {
       tc::CountArgs a{g.n, g.m, g.offsets, g.cols, nullptr, nullptr, r.tri, static_cast<int64_t>(r.T)};
       if (e == cudaSuccess) e = tc::launch_count(ctx, tc::MODE_LIST_WRITE, a, w, st);

@@ -27,7 +27,7 @@ SparsifyWs carve_sparsify(Carver& c, int32_t n, int64_t m) {
   w.offsets = c.take<int64_t>(static_cast<size_t>(n) + 1);
   w.cols = c.take<int32_t>(static_cast<size_t>(m > 0 ? m : 1));
   w.scan = carve_scan(c, n);
-  w.count = carve_count(c, n, false);
+  w.count = carve_count(c, n, m, false);
   return w;
 }
 
