@@ -136,6 +136,7 @@ struct BatchSmem {
   int32_t salt[32];       // tile kernel: filter salt (chunk lane of v)
   uint32_t cnt[32];       // matches of the edge
   uint32_t erun[32];      // listing: triples of the edge written so far
+  int64_t ebase[32];      // listing: output offset of the edge
   int32_t qw[64];         // filter survivors: candidate id ...
   int32_t qs[64];         // ... and its edge
   uint8_t own[kOwnCap];   // flattened position -> edge, short lists
@@ -145,7 +146,8 @@ struct BatchSmem {
 // the short lists, *is_short whether this lane's list is one of them, *len its length.
 __device__ __forceinline__ void batch_setup(BatchSmem& bs, const CountArgs& a, const CountWs& ws, int32_t u,
                                             bool act, int64_t eg, int32_t salt, int32_t lo, int32_t vlen,
-                                            int& tot, bool& is_short, int32_t& len, uint32_t* err, bool list_write) {
+                                            int& tot, bool& is_short, int32_t& len, uint32_t* err, bool list_write,
+                                            uint32_t erun0 = 0) {
   const int lane = lane_id();
   int64_t ub = 0;
   len = 0;
@@ -164,7 +166,8 @@ __device__ __forceinline__ void batch_setup(BatchSmem& bs, const CountArgs& a, c
   bs.len[lane] = vlen;
   bs.salt[lane] = salt;
   bs.cnt[lane] = 0;
-  bs.erun[lane] = 0;
+  bs.erun[lane] = erun0;
+  if (list_write) bs.ebase[lane] = act ? ws.eoff[eg] : 0;
   for (int i = 0; i < slen; ++i) bs.own[excl + i] = static_cast<uint8_t>(lane);
   __syncwarp();
 }
@@ -178,7 +181,7 @@ __device__ __forceinline__ void write_triples(BatchSmem& bs, bool has, bool f, i
   if (!fm) return;
   const unsigned same = __match_any_sync(FULL, has ? s : 32 + lane);
   if (f) {
-    const int64_t idx = ws.eoff[bs.eg[s]] + bs.erun[s] + __popc(fm & same & lanemask_lt());
+    const int64_t idx = bs.ebase[s] + bs.erun[s] + __popc(fm & same & lanemask_lt());
     if (idx < a.cap) {
       a.tri[3 * idx] = v;
       a.tri[3 * idx + 1] = bs.u[s];
@@ -503,13 +506,16 @@ __device__ __forceinline__ void hash_record(BatchSmem& bs, uint32_t* slot_cnt, b
 template <int MODE>
 __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab, uint32_t* slot_cnt, int32_t lo,
                                                int32_t hi, int32_t u, bool act, int64_t eg, int32_t v,
-                                               const CountArgs& a, const CountWs& ws, uint32_t* err) {
+                                               const CountArgs& a, const CountWs& ws, uint32_t* err,
+                                               bool chunked, bool first_chunk) {
   constexpr int L = HashCfg<MODE>::kLog2;
   const int lane = lane_id();
   int tot;
   bool is_short;
   int32_t len;
-  batch_setup(bs, a, ws, u, act, eg, 0, 0, 0, tot, is_short, len, err, MODE == MODE_LIST_WRITE);
+  // listing a vertex hashed in several chunks: an edge's triples continue where the last chunk stopped
+  const uint32_t erun0 = (MODE == MODE_LIST_WRITE && chunked && !first_chunk && act) ? ws.erun[eg] : 0u;
+  batch_setup(bs, a, ws, u, act, eg, 0, 0, 0, tot, is_short, len, err, MODE == MODE_LIST_WRITE, erun0);
   for (int32_t p0 = 0; p0 < tot; p0 += 32 * kUnroll) {
     int32_t w[kUnroll];
     int s[kUnroll];
@@ -552,6 +558,7 @@ __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab
     }
   }
   __syncwarp();
+  if (MODE == MODE_LIST_WRITE && chunked && act) ws.erun[eg] = bs.erun[lane];
   return act ? bs.cnt[lane] : 0u;
 }
 
@@ -594,7 +601,8 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
         const int nb = static_cast<int>(min64(32, dv - ub));
         const bool act = lane < nb;
         const int32_t u = act ? a.cols[b + ub + lane] : 0;
-        const uint32_t c = hash_batch<MODE>(s_b[wid], tab, slot_cnt, lo, hi, u, act, b + ub + lane, v, a, ws, err);
+        const uint32_t c = hash_batch<MODE>(s_b[wid], tab, slot_cnt, lo, hi, u, act, b + ub + lane, v, a, ws, err,
+                                            dv > H::kCap, c0 == 0);
         cv += c;
         if (act && (MODE == MODE_LOCAL || MODE == MODE_LIST_COUNT) && ws.ecount) {
           // the same lane holds the same edge in every chunk
@@ -654,6 +662,14 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
     k_count_tile<MODE><<<tgrid, kTileWarps * 32, 0, s>>>(a, ws, ctx->d_err);
   }
   const size_t smem = HashCfg<MODE>::kBytes;
+  // static plus dynamic shared memory exceeds the 48 KB default: opt in once per device
+  static bool attr_set[64] = {false};
+  if (ctx->device >= 0 && ctx->device < 64 && !attr_set[ctx->device]) {
+    const cudaError_t e = cudaFuncSetAttribute(k_count_block<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    attr_set[ctx->device] = true;
+  }
   const int bgrid = static_cast<int>(min64(
       persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_block<MODE>), kBlockWarps * 32, smem),
       max64(1, a.m / (a.tile_max + 1))));  // at most m / (tile_max + 1) lists go to this kernel
@@ -673,6 +689,7 @@ CountWs carve_count(Carver& c, int32_t n, int64_t m, bool listing) {
   w.counters = c.take<uint32_t>(4);
   if (listing) {
     w.ecount = c.take<int32_t>(static_cast<size_t>(m > 0 ? m : 1));
+    w.erun = c.take<uint32_t>(static_cast<size_t>(m > 0 ? m : 1));
     w.eoff = c.take<int64_t>(static_cast<size_t>(m) + 1);
     w.scan = carve_scan(c, m);
   }

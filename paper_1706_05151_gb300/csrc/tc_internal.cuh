@@ -105,6 +105,7 @@ struct CountWs {
   int32_t* big_queue;   // vertices left to the block kernel
   uint32_t* counters;   // [0] queue length, [1] vertex cursor of the tile kernel, [2..3] spare
   int32_t* ecount;      // listing: triangles per oriented edge (m)
+  uint32_t* erun;       // listing: triples written per edge, carried across hash chunks (m)
   int64_t* eoff;        // listing: output offset per oriented edge (m + 1; eoff[m] = T)
   ScanWs scan;          // listing: scan over the m edge counts
 };

@@ -70,11 +70,15 @@ __global__ void __launch_bounds__(1024) k_scan_sums(int64_t* sums, int64_t tiles
   if (threadIdx.x == 0) sums[tiles] = carry;
 }
 
+// Padded index into the shared tile: one spare slot per kScanItems entries, so
+// a thread's kScanItems consecutive int64 fall in different banks than its neighbours'.
+__device__ __forceinline__ int pad(int i) { return i + i / kScanItems; }
+
 template <class T>
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const T* __restrict__ in, int64_t n,
                                                             const int64_t* __restrict__ sums,
                                                             int64_t* __restrict__ out, int64_t tiles) {
-  __shared__ int64_t tile[kScanTile];
+  __shared__ int64_t tile[kScanTile + kScanTile / kScanItems];
   __shared__ int64_t warp_sums[32];
   __shared__ int64_t total;
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile;
@@ -82,7 +86,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const T* __restrict_
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     int idx = k * kScanThreads + threadIdx.x;
-    tile[idx] = load_or_zero(in, base + idx, n);
+    tile[pad(idx)] = load_or_zero(in, base + idx, n);
   }
   __syncthreads();
   int64_t local[kScanItems];
@@ -90,16 +94,16 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const T* __restrict_
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     local[k] = s;
-    s += tile[threadIdx.x * kScanItems + k];
+    s += tile[pad(threadIdx.x * kScanItems + k)];
   }
   int64_t pre = block_exclusive(s, warp_sums, &total) + sums[blockIdx.x];
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) tile[threadIdx.x * kScanItems + k] = pre + local[k];
+  for (int k = 0; k < kScanItems; ++k) tile[pad(threadIdx.x * kScanItems + k)] = pre + local[k];
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     int64_t i = base + k * kScanThreads + threadIdx.x;
-    if (i < n) out[i] = tile[k * kScanThreads + threadIdx.x];
+    if (i < n) out[i] = tile[pad(k * kScanThreads + threadIdx.x)];
   }
   if (blockIdx.x == tiles - 1 && threadIdx.x == 0) out[n] = sums[tiles];
 }

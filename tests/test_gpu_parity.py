@@ -304,3 +304,17 @@ def test_autotuner_records_a_candidate(tc, tmp_path):
         assert tc.count(g) == oracle.count(n, synth.rmat(13, 16, 42))["T"]
     finally:
         tc.default_context().set_tuning(0, 1)
+
+
+def test_listing_of_lists_longer_than_one_hash_chunk(tc):
+    # K_2600: N_v up to 2599 ids is hashed in two chunks (2048 ids each) by the
+    # block kernel; every triangle must be listed once, in the same order every run
+    n = 2600
+    e = synth.shuffle_edges(synth.complete(n), 12)
+    g = tc.orient(to_dev(e), n)
+    T, tv, cc, tri = tc.analyze(g)
+    assert T == math.comb(n, 3) and len(tri) == T
+    t = tri.to(torch.int64)
+    assert bool(torch.all((t[:, 0] != t[:, 1]) & (t[:, 1] != t[:, 2]) & (t[:, 0] != t[:, 2])))
+    assert int(torch.unique(torch.sort(tri, dim=1).values, dim=0).shape[0]) == T
+    assert torch.equal(tc.list_triangles(g), tri)
