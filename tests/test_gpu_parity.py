@@ -307,14 +307,19 @@ def test_autotuner_records_a_candidate(tc, tmp_path):
 
 
 def test_listing_of_lists_longer_than_one_hash_chunk(tc):
-    # K_2600: N_v up to 2599 ids is hashed in two chunks (2048 ids each) by the
-    # block kernel; every triangle must be listed once, in the same order every run
-    n = 2600
+    # K_2100: the write pass hashes N_v (up to 2099 ids) in two chunks of 2048;
+    # every triangle must be listed once, in the same order every run.  All
+    # degrees are equal, so the order is by id and each triple is v < u < w.
+    n = 2100
     e = synth.shuffle_edges(synth.complete(n), 12)
     g = tc.orient(to_dev(e), n)
     T, tv, cc, tri = tc.analyze(g)
     assert T == math.comb(n, 3) and len(tri) == T
     t = tri.to(torch.int64)
-    assert bool(torch.all((t[:, 0] != t[:, 1]) & (t[:, 1] != t[:, 2]) & (t[:, 0] != t[:, 2])))
-    assert int(torch.unique(torch.sort(tri, dim=1).values, dim=0).shape[0]) == T
+    assert bool(torch.all((t[:, 0] < t[:, 1]) & (t[:, 1] < t[:, 2])))
+    key = (t[:, 0] * n + t[:, 1]) * n + t[:, 2]
+    del t
+    key = torch.sort(key).values
+    assert bool(torch.all(key[1:] > key[:-1]))  # all distinct, so all C(n, 3) present
+    del key
     assert torch.equal(tc.list_triangles(g), tri)
