@@ -172,6 +172,18 @@ __device__ __forceinline__ void batch_setup(BatchSmem& bs, const CountArgs& a, c
   __syncwarp();
 }
 
+// Lanes in this lane's run of equal keys (runs are contiguous lane ranges).
+__device__ __forceinline__ unsigned run_mask(int key) {
+  const int lane = lane_id();
+  const int prev = __shfl_up_sync(FULL, key, 1);
+  const unsigned heads = __ballot_sync(FULL, lane == 0 || key != prev);
+  const unsigned upto = lane == 31 ? FULL : (2u << lane) - 1u;   // lanes <= me
+  const int head = 31 - __clz(heads & upto);
+  const unsigned after = heads & ~upto;
+  const unsigned below_next = after ? (1u << (__ffs(after) - 1)) - 1u : FULL;
+  return below_next & ~((1u << head) - 1u);
+}
+
 // Listing: write this lane's triple (if f) at its edge's offset plus the
 // edge's running count; lanes of one edge are contiguous and in candidate order.
 __device__ __forceinline__ void write_triples(BatchSmem& bs, bool has, bool f, int s, int32_t v, int32_t w,
@@ -179,7 +191,7 @@ __device__ __forceinline__ void write_triples(BatchSmem& bs, bool has, bool f, i
   const int lane = lane_id();
   const unsigned fm = __ballot_sync(FULL, f);
   if (!fm) return;
-  const unsigned same = __match_any_sync(FULL, has ? s : 32 + lane);
+  const unsigned same = run_mask(has ? s : 32 + lane);
   if (f) {
     const int64_t idx = bs.ebase[s] + bs.erun[s] + __popc(fm & same & lanemask_lt());
     if (idx < a.cap) {
