@@ -202,8 +202,9 @@ def bench_batched(tc, ctx, dev, args, rank):
     tuned = None
     if not args.no_tune:
         from paper_1706_05151_gb300 import autotune
-        best, times = autotune.tune(union, ctx, record=False)
-        tuned = {"tile_max": best, "count_ms_by_tile_max": {str(k): round(v, 3) for k, v in times.items()}}
+        best, times, hub, hub_times = autotune.tune(union, ctx, record=False)
+        tuned = {"tile_max": best, "count_ms_by_tile_max": {str(k): round(v, 3) for k, v in times.items()},
+                 "hub_min": hub, "count_ms_by_hub_min": {str(k): round(v, 3) for k, v in hub_times.items()}}
     del union
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -213,6 +214,20 @@ def bench_batched(tc, ctx, dev, args, rank):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     batched_ms = e0.elapsed_time(e1) / args.batch_steps
+    # the same sequence recorded once as a CUDA graph and replayed (tc_capture_begin / tc_capture_end)
+    cap = tc.CapturedBatch(b, True, ctx)
+    cap.replay(stream)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(args.batch_steps):
+        cap.replay(stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    captured_ms = e0.elapsed_time(e1) / args.batch_steps
+    captured_same = bool(torch.equal(cap.totals, totals)) and bool(torch.equal(cap.tv[:N], tv))
+    captured_kernels = cap.kernels
+    cap.close()
+    del cap
     # per graph: one tc_orient + tc_count_local launch sequence per graph, no host wait in between
     lib = ctx.lib
     offsets = torch.empty(N + G, dtype=torch.int64, device=dev)
@@ -244,7 +259,8 @@ def bench_batched(tc, ctx, dev, args, rank):
                                          ctypes.c_void_p(tvp + 8 * int(vb[g])), None, ctypes.c_void_p(wsp), wsn, hs))
 
     ctx.set_async(True)
-    ctx.set_tuning(0, 1)  # the plain per-graph form runs with the default threshold
+    ctx.set_tuning(0, 1)  # the plain per-graph form runs with the default thresholds
+    ctx.set_hub_min(0)
     try:
         per_graph()  # warm-up
         torch.cuda.synchronize(dev)
@@ -260,6 +276,8 @@ def bench_batched(tc, ctx, dev, args, rank):
     return {"workload": f"{G} Chung-Lu graphs (gamma 2.1), n log-uniform in [100, 1e5], mean degree U[8, 64]",
             "graphs": G, "vertices": N, "edges": E, "triangles": int(totals.sum().item()),
             "batched_ms": batched_ms, "per_graph_ms": per_graph_ms, "speedup": per_graph_ms / batched_ms,
+            "captured_ms": captured_ms, "captured_speedup": per_graph_ms / captured_ms,
+            "captured_kernels_per_replay": captured_kernels, "captured_results_equal": captured_same,
             "batched_edges_per_s": E / (batched_ms * 1e-3), "results_equal": same, "autotune": tuned}
 
 
@@ -422,8 +440,9 @@ def main():
     tuned = None
     if not args.no_tune:  # pick the cost-bin threshold on this graph (outside the timed region)
         from paper_1706_05151_gb300 import autotune
-        best, times = autotune.tune(g, ctx, record=False)
-        tuned = {"tile_max": best, "count_ms_by_tile_max": {str(k): round(v, 3) for k, v in times.items()}}
+        best, times, hub, hub_times = autotune.tune(g, ctx, record=False)
+        tuned = {"tile_max": best, "count_ms_by_tile_max": {str(k): round(v, 3) for k, v in times.items()},
+                 "hub_min": hub, "count_ms_by_hub_min": {str(k): round(v, 3) for k, v in hub_times.items()}}
         g, T, tv, cc, tri, sp = step()
     W = int((g.deg.to(torch.int64) * g.dhat.to(torch.int64)).sum().item())
     assert int(tv.sum().item()) == 3 * T and len(tri) == T
@@ -509,7 +528,8 @@ def main():
 
     # ---- roofline of the intersection kernel (per-vertex counting pass) ----
     peak, peak_src = load_peaks()
-    inter_ms = sum(stages.get(k, (0.0, 0))[0] for k in ("local.tile", "local.block"))
+    # every kernel of the per-vertex counting pass: tile, block, hub preparation and hub kernels
+    inter_ms = sum(stages.get(k, (0.0, 0))[0] for k in ("local.tile", "local.block", "local.hub_prep", "local.hub"))
     inter_calls = max(stages.get("local.tile", (0.0, 0))[1], 1)
     inter_avg_ms = inter_ms / inter_calls
     b_alg = 4 * W + 4 * m + 8 * (n + 1)
@@ -541,7 +561,7 @@ def main():
                        "autotune": tuned},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_count_tile+k_count_block, per-vertex pass of tc_analyze",
+                         "kernel": "k_count_tile+k_count_block+hub side, per-vertex pass of tc_analyze",
                          "algorithmic_bytes": b_alg, "avg_launch_ms": inter_avg_ms, "peak_source": peak_src},
             "e2e": {"value": m_total / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},

@@ -107,11 +107,24 @@ const char* tc_version(void);
  * Tuning (no counterpart in the paper; the paper balances processors with the
  * cost functions of Table "lbscheme", this balances one GPU).  tile_max: apex
  * vertices with |N_v| > tile_max are counted one thread block per vertex, the
- * others 32 to a warp (0 = 512, the largest allowed).  grid_div: persistent
+ * others 32 to a warp (0 = 256, the warp tile's capacity; values up to 512 are
+ * accepted and act as 256).  grid_div: persistent
  * grids use 1/grid_div of the GPU's resident capacity (0 or 1 = all of it),
  * leaving room for work on other streams.  Results do not depend on either.
  */
 tc_status tc_ctx_set_tuning(tc_ctx* ctx, int32_t tile_max, int32_t grid_div);
+
+/*
+ * Hub side of the intersection (a cost split; results never depend on it).
+ * Theorem 2's work for an oriented edge (v, u) is reading N_v and N_u; the
+ * counting kernels keep the apex list N_v on chip and stream N_u.  When N_u
+ * is long (at least hub_min ids) and longer than N_v, the edge is instead
+ * counted from u's side: N_u is hashed into shared memory once for all such
+ * edges of u and each short N_v is streamed, so the per-edge read falls from
+ * |N_u| to |N_v|.  hub_min = 0 restores the default (64); -1 turns the hub
+ * side off; other negative values give TC_ERR_INVALID_ARG.
+ */
+tc_status tc_ctx_set_hub_min(tc_ctx* ctx, int32_t hub_min);
 
 /*
  * Per-stage timing and launch accounting (no counterpart in the paper; it
@@ -261,6 +274,37 @@ tc_status tc_sparsify_count(tc_ctx* ctx, const tc_graph* g, double q, uint64_t s
 tc_status tc_batch(tc_ctx* ctx, int32_t G, int32_t N, int64_t E, const int64_t* vbase_dev, const int64_t* ebase_dev,
                    const int32_t* edges_dev, int64_t* offsets, int32_t* cols, int32_t* deg, int32_t* dhat,
                    uint64_t* totals_dev, int64_t* tv_dev, void* ws, size_t ws_bytes, tc_stream stream);
+
+/* ---- captured launch sequences ------------------------------------------------ */
+
+/*
+ * CUDA-graph capture of a sequence of calls (no counterpart in the paper).  A
+ * sequence such as tc_batch (orientation + counting of thousands of graphs,
+ * about twenty kernels) or tc_orient + tc_count is recorded once and replayed
+ * with one cudaGraphLaunch, which removes the per-kernel launch cost from the
+ * replays.  A replay re-runs the recorded kernels on the SAME device buffers
+ * and sizes; the caller refills the inputs in place between replays.
+ *
+ * tc_capture_begin starts stream capture on `stream` (a created stream, not
+ * the legacy default stream) and puts ctx in capture mode until
+ * tc_capture_end: calls only enqueue (as in asynchronous mode) and profiling
+ * events are not recorded.  Calls that must synchronize to return a result on
+ * the host (tc_list, tc_analyze) return TC_ERR_INVALID_ARG while capturing.
+ * Input errors found on the device during a replay accumulate in the
+ * context's error word: read them with tc_ctx_status.
+ * tc_capture_end ends the capture and instantiates it into *out (owned by the
+ * caller, freed by tc_exec_destroy); on a failed call inside the capture it
+ * returns that failure and discards the capture.
+ */
+typedef struct tc_exec tc_exec;
+
+tc_status tc_capture_begin(tc_ctx* ctx, tc_stream stream);
+tc_status tc_capture_end(tc_ctx* ctx, tc_stream stream, tc_exec** out);
+/* Replay the captured sequence on `stream` (any stream of the same device). */
+tc_status tc_exec_launch(tc_exec* x, tc_stream stream);
+/* Kernels in one replay (kernel nodes of the captured graph). */
+int64_t tc_exec_kernels(const tc_exec* x);
+void tc_exec_destroy(tc_exec* x);
 
 /* ---- serving ----------------------------------------------------------------- */
 

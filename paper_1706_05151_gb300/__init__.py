@@ -37,8 +37,9 @@ EXPORTS = ["tc_ctx_create", "tc_ctx_destroy", "tc_ctx_set_async", "tc_ctx_status
            "tc_batch", "tc_serve_create", "tc_serve_destroy", "tc_serve_last_error", "tc_serve_add_graph",
            "tc_serve_remove_graph", "tc_serve_submit", "tc_serve_poll", "tc_serve_wait", "tc_serve_release",
            "tc_serve_stats",
-           "tc_ctx_set_tuning", "tc_ctx_set_profiling", "tc_ctx_stage_count", "tc_ctx_stage", "tc_ctx_reset_stats", "tc_ctx_launches",
-           "tc_count_static"]
+           "tc_ctx_set_tuning", "tc_ctx_set_hub_min", "tc_ctx_set_profiling", "tc_ctx_stage_count", "tc_ctx_stage", "tc_ctx_reset_stats", "tc_ctx_launches",
+           "tc_count_static", "tc_capture_begin", "tc_capture_end", "tc_exec_launch", "tc_exec_kernels",
+           "tc_exec_destroy"]
 
 
 class TcError(RuntimeError):
@@ -106,6 +107,11 @@ def load_library(path: str = LIB_PATH):
             "tc_list": (i32, [vp, G, vp, i64, ctypes.POINTER(i64), vp, sz, vp]),
             "tc_analyze": (i32, [vp, G, vp, vp, vp, vp, i64, ctypes.POINTER(i64), vp, sz, vp]),
             "tc_batch": (i32, [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+            "tc_capture_begin": (i32, [vp, vp]),
+            "tc_capture_end": (i32, [vp, vp, ctypes.POINTER(vp)]),
+            "tc_exec_launch": (i32, [vp, vp]),
+            "tc_exec_kernels": (i64, [vp]),
+            "tc_exec_destroy": (None, [vp]),
             "tc_sparsify_count": (i32, [vp, G, ctypes.c_double, u64, vp, vp, vp, sz, vp]),
             "tc_serve_create": (i32, [ctypes.c_int, ctypes.POINTER(TcServeConfig), vp, sz, ctypes.POINTER(vp)]),
             "tc_serve_destroy": (None, [vp]),
@@ -117,6 +123,7 @@ def load_library(path: str = LIB_PATH):
             "tc_serve_wait": (i32, [vp, i64, i64, ctypes.POINTER(TcResult)]),
             "tc_serve_release": (i32, [vp, i64]),
             "tc_serve_stats": (i32, [vp, ctypes.POINTER(TcServeStats)]),
+            "tc_ctx_set_hub_min": (i32, [vp, i32]),
             "tc_ctx_set_tuning": (i32, [vp, i32, i32]),
             "tc_ctx_set_profiling": (i32, [vp, ctypes.c_int]),
             "tc_ctx_stage_count": (ctypes.c_int, [vp]),
@@ -184,6 +191,10 @@ class Context:
     def set_tuning(self, tile_max: int = 0, grid_div: int = 1):
         """tc_ctx_set_tuning: tile/block threshold on |N_v| and the share of the GPU per launch."""
         self.check(self.lib.tc_ctx_set_tuning(self.handle, int(tile_max), int(grid_div)))
+
+    def set_hub_min(self, hub_min: int = 0):
+        """tc_ctx_set_hub_min: lists of >= hub_min ids take their longer-list in-edges (0 default, -1 off)."""
+        self.check(self.lib.tc_ctx_set_hub_min(self.handle, hub_min))
 
     def set_profiling(self, on: bool):
         self.check(self.lib.tc_ctx_set_profiling(self.handle, 1 if on else 0))
@@ -390,6 +401,66 @@ def batch(b: Batch, local: bool = True, ctx: Context | None = None):
                                _ptr(offsets), _ptr(cols), _ptr(deg), _ptr(dhat), _ptr(totals), _ptr(tv),
                                _ptr(ws), ws.numel(), _stream(dev)))
     return totals, (tv[:N] if tv is not None else None), Graph(N, E, offsets, cols[:E], deg[:N], dhat[:N])
+
+
+class CapturedBatch:
+    """tc_batch recorded once as a CUDA graph (tc_capture_begin / tc_capture_end)
+    and replayed with one launch per call.
+
+    Every buffer the sequence touches -- outputs and a workspace of its own -- is
+    allocated here, before the capture, and kept alive by this object.  A replay
+    re-runs the recorded kernels on b's device buffers: refill b.edges (and
+    b.vbase, b.ebase, for graphs of the same G, N and E) in place between replays.
+    """
+
+    def __init__(self, b: Batch, local: bool = True, ctx: Context | None = None):
+        self.ctx = ctx = ctx or default_context()
+        dev = ctx.device
+        self.b = b
+        N, E = b.N, b.E
+        self.offsets = torch.empty(N + 1, dtype=torch.int64, device=dev)
+        self.cols = torch.empty(max(E, 1), dtype=torch.int32, device=dev)
+        self.deg = torch.empty(max(N, 1), dtype=torch.int32, device=dev)
+        self.dhat = torch.empty(max(N, 1), dtype=torch.int32, device=dev)
+        self.totals = torch.empty(b.G, dtype=torch.int64, device=dev)
+        self.tv = torch.empty(max(N, 1), dtype=torch.int64, device=dev) if local else None
+        self.ws = torch.empty(max(ctx.workspace_size(TC_OP_BATCH, N, E), 1), dtype=torch.uint8, device=dev)
+        self.handle = None
+        stream = torch.cuda.Stream(dev)
+        stream.wait_stream(torch.cuda.current_stream(dev))
+        lib, h = ctx.lib, ctx.handle
+        sp = ctypes.c_void_p(stream.cuda_stream)
+        ctx.check(lib.tc_capture_begin(h, sp))
+        st = lib.tc_batch(h, b.G, N, E, _ptr(b.vbase), _ptr(b.ebase), _ptr(b.edges) if E else None,
+                          _ptr(self.offsets), _ptr(self.cols), _ptr(self.deg), _ptr(self.dhat), _ptr(self.totals),
+                          _ptr(self.tv), _ptr(self.ws), self.ws.numel(), sp)
+        x = vp()
+        st_end = lib.tc_capture_end(h, sp, ctypes.byref(x))
+        ctx.check(st if st != 0 else st_end)
+        self.handle = x
+        self.kernels = int(lib.tc_exec_kernels(x))
+
+    def replay(self, stream: torch.cuda.Stream | None = None):
+        """Enqueue one replay on `stream` (default: the current stream)."""
+        s = stream or torch.cuda.current_stream(self.ctx.device)
+        self.ctx.check(self.ctx.lib.tc_exec_launch(self.handle, ctypes.c_void_p(s.cuda_stream)))
+
+    def result(self):
+        """(totals int64[G], tv int64[N] or None, the oriented union as a Graph) of the last replay."""
+        N, E = self.b.N, self.b.E
+        return (self.totals, self.tv[:N] if self.tv is not None else None,
+                Graph(N, E, self.offsets, self.cols[:E], self.deg[:N], self.dhat[:N]))
+
+    def close(self):
+        if self.handle is not None:
+            self.ctx.lib.tc_exec_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class _DeviceArray:

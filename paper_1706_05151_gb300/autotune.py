@@ -1,14 +1,16 @@
-"""Autotuner for the counting kernels' cost bin.
+"""Autotuner for the counting kernels' cost bins.
 
-The one threshold that changes how work is split is `tile_max`: apex vertices
-whose oriented list N_v has more than tile_max ids are counted one thread
-block per vertex, the others 32 to a warp.  Skewed graphs (R-MAT, Chung-Lu)
-want a low threshold, so that the few heavy vertices do not leave one warp
-working while the rest of the GPU idles; graphs with short lists (PA, ER) do
-not care.  The tuner times tc_count on the graph itself for each candidate and
-records the winner per graph-shape class in a JSON table, so that later runs
-on graphs of the same shape start from it.  Results never depend on the
-threshold; only the time does.
+Two thresholds change how work is split.  `tile_max`: apex vertices whose
+oriented list N_v has more than tile_max ids are counted one thread block per
+vertex, the others 32 to a warp.  Skewed graphs (R-MAT, Chung-Lu) want a low
+threshold, so that the few heavy vertices do not leave one warp working while
+the rest of the GPU idles; graphs with short lists (PA, ER) do not care.
+`hub_min`: an edge (v, u) whose N_u has at least hub_min ids and more than N_v
+is counted from u's side (N_u hashed once, the shorter N_v streamed).  The
+tuner times tc_count on the graph itself for each candidate of tile_max, then
+of hub_min, and records the winners per graph-shape class in a JSON table, so
+that later runs on graphs of the same shape start from them.  Results never
+depend on either threshold; only the time does.
 """
 from __future__ import annotations
 
@@ -18,7 +20,8 @@ import os
 
 import torch
 
-CANDIDATES = (32, 64, 128, 256, 512)
+CANDIDATES = (32, 64, 128, 256)
+HUB_CANDIDATES = (-1, 32, 64, 128, 256)   # -1: hub side off
 TABLE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
 
 
@@ -46,8 +49,9 @@ def save_table(table: dict, path: str = TABLE_PATH):
     os.replace(tmp, path)
 
 
-def time_count(tc, g, ctx, tile_max: int, repeats: int) -> float:
+def time_count(tc, g, ctx, tile_max: int, repeats: int, hub_min: int = 0) -> float:
     ctx.set_tuning(tile_max, 1)
+    ctx.set_hub_min(hub_min)
     out = torch.empty(1, dtype=torch.int64, device=ctx.device)
     tc.count(g, ctx, out=out)  # warm-up
     stream = torch.cuda.current_stream(ctx.device)
@@ -60,29 +64,38 @@ def time_count(tc, g, ctx, tile_max: int, repeats: int) -> float:
     return e0.elapsed_time(e1) / repeats
 
 
-def tune(g, ctx=None, candidates=CANDIDATES, repeats: int = 3, record: bool = True, path: str = TABLE_PATH):
-    """Time every candidate threshold on g; apply and (optionally) record the best.
+def tune(g, ctx=None, candidates=CANDIDATES, repeats: int = 3, record: bool = True, path: str = TABLE_PATH,
+         hub_candidates=HUB_CANDIDATES):
+    """Time every candidate tile_max on g, then every hub_min at the best
+    tile_max; apply and (optionally) record the best pair.
 
-    Returns (best tile_max, {candidate: ms}).
+    Returns (best tile_max, {candidate: ms}, best hub_min, {candidate: ms}).
     """
     import paper_1706_05151_gb300 as tc
     ctx = ctx or tc.default_context()
     times = {t: time_count(tc, g, ctx, t, repeats) for t in candidates}
     best = min(times, key=times.get)
+    hub_times = {h: time_count(tc, g, ctx, best, repeats, h) for h in hub_candidates}
+    best_hub = min(hub_times, key=hub_times.get)
     ctx.set_tuning(best, 1)
+    ctx.set_hub_min(best_hub)
     if record:
         table = load_table(path)
         table[shape_class(g)] = {"tile_max": best, "ms": {str(k): round(v, 4) for k, v in times.items()},
+                                 "hub_min": best_hub,
+                                 "hub_ms": {str(k): round(v, 4) for k, v in hub_times.items()},
                                  "n": g.n, "m": g.m}
         save_table(table, path)
-    return best, times
+    return best, times, best_hub, hub_times
 
 
-def apply(g, ctx=None, path: str = TABLE_PATH) -> int:
-    """Use the recorded threshold for g's shape class (the default if none)."""
+def apply(g, ctx=None, path: str = TABLE_PATH):
+    """Use the recorded thresholds for g's shape class (the defaults if none); returns (tile_max, hub_min)."""
     import paper_1706_05151_gb300 as tc
     ctx = ctx or tc.default_context()
     rec = load_table(path).get(shape_class(g))
     best = int(rec["tile_max"]) if rec else 0
+    hub = int(rec.get("hub_min", 0)) if rec else 0
     ctx.set_tuning(best, 1)
-    return best
+    ctx.set_hub_min(hub)
+    return best, hub

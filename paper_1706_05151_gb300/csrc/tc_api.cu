@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "tc_internal.cuh"
 
@@ -21,6 +22,8 @@ tc_status fail(tc_ctx* ctx, tc_status st, const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(ctx->last_error, sizeof(ctx->last_error), fmt, ap);
     va_end(ap);
+    // a call that fails inside a capture spoils the recorded sequence
+    if (ctx->capturing && st != TC_OK && ctx->capture_status == TC_OK) ctx->capture_status = st;
   }
   return st;
 }
@@ -113,7 +116,7 @@ void resolve_stages(Ctx* ctx) {
 namespace tc {
 
 Stage::Stage(Ctx* ctx, cudaStream_t s, const char* name) : ctx_(ctx), s_(s) {
-  if (!ctx->prof.on) return;
+  if (!ctx->prof.on || ctx->capturing) return;
   auto& t = ctx->prof.totals;
   for (size_t i = 0; i < t.size(); ++i)
     if (t[i].name == name) index_ = static_cast<int>(i);
@@ -192,18 +195,26 @@ void tc_ctx_destroy(tc_ctx* ctx) {
 
 tc_status tc_ctx_set_async(tc_ctx* ctx, int async) {
   if (!ctx) return TC_ERR_INVALID_ARG;
+  if (ctx->capturing) return fail(ctx, TC_ERR_INVALID_ARG, "capture in progress");
   ctx->async = async ? 1 : 0;
   return TC_OK;
 }
 
 tc_status tc_ctx_status(tc_ctx* ctx, tc_stream stream) {
   if (!ctx) return TC_ERR_INVALID_ARG;
+  if (ctx->capturing) return fail(ctx, TC_ERR_INVALID_ARG, "cannot synchronize while capturing");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "status");
   return status_from_bits(ctx, *ctx->h_err);
+}
+
+tc_status tc_ctx_set_hub_min(tc_ctx* ctx, int32_t hub_min) {
+  if (!ctx || hub_min < -1) return TC_ERR_INVALID_ARG;
+  ctx->hub_min = hub_min;
+  return TC_OK;
 }
 
 tc_status tc_ctx_set_tuning(tc_ctx* ctx, int32_t tile_max, int32_t grid_div) {
@@ -352,6 +363,7 @@ tc_status tc_list_write(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_
 tc_status tc_list(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_t cap, int64_t* count_out, void* ws,
                   size_t ws_bytes, tc_stream stream) {
   if (!ctx) return TC_ERR_INVALID_ARG;
+  if (ctx->capturing) return fail(ctx, TC_ERR_INVALID_ARG, "tc_list synchronizes: not capturable");
   if (!count_out) return fail(ctx, TC_ERR_INVALID_ARG, "count_out is NULL");
   tc_status st = check_graph(ctx, g);
   if (st != TC_OK) return st;
@@ -380,6 +392,7 @@ tc_status tc_analyze(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, int64_
                      int32_t* tri_dev, int64_t cap, int64_t* count_out, void* ws, size_t ws_bytes, tc_stream stream) {
   tc_status st = check_graph(ctx, g);
   if (st != TC_OK) return st;
+  if (ctx->capturing) return fail(ctx, TC_ERR_INVALID_ARG, "tc_analyze synchronizes: not capturable");
   if (!total_dev || !tv_dev || !count_out) return fail(ctx, TC_ERR_INVALID_ARG, "NULL output");
   if (cc_dev && g->n > 0 && !g->deg) return fail(ctx, TC_ERR_INVALID_ARG, "clustering needs g->deg");
   if (cap < 0 || (cap > 0 && !tri_dev)) return fail(ctx, TC_ERR_INVALID_ARG, "bad output buffer");
@@ -469,6 +482,89 @@ tc_status tc_sparsify_count(tc_ctx* ctx, const tc_graph* g, double q, uint64_t s
     e = tc::launch_count(ctx, tc::MODE_COUNT, a, w.count, s);
   }
   return finish(ctx, s, e);
+}
+
+// ---- captured launch sequences ----------------------------------------------
+
+struct tc_exec {
+  int device = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;
+};
+
+tc_status tc_capture_begin(tc_ctx* ctx, tc_stream stream) {
+  if (!ctx) return TC_ERR_INVALID_ARG;
+  if (!stream) return fail(ctx, TC_ERR_INVALID_ARG, "the legacy default stream cannot be captured");
+  if (ctx->capturing) return fail(ctx, TC_ERR_INVALID_ARG, "capture already in progress");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, TC_ERR_CUDA, "cudaSetDevice failed");
+  cudaError_t e = cudaStreamBeginCapture(static_cast<cudaStream_t>(stream), cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "begin capture");
+  ctx->capturing = 1;
+  ctx->capture_status = TC_OK;
+  ctx->saved_async = ctx->async;
+  ctx->async = 1;
+  return TC_OK;
+}
+
+tc_status tc_capture_end(tc_ctx* ctx, tc_stream stream, tc_exec** out) {
+  if (!ctx) return TC_ERR_INVALID_ARG;
+  if (!ctx->capturing) return fail(ctx, TC_ERR_INVALID_ARG, "no capture in progress");
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(static_cast<cudaStream_t>(stream), &graph);
+  ctx->capturing = 0;
+  ctx->async = ctx->saved_async;
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(ctx, e, "end capture");
+  }
+  if (ctx->capture_status != TC_OK) {  // last_error still holds the failed call's message
+    cudaGraphDestroy(graph);
+    return static_cast<tc_status>(ctx->capture_status);
+  }
+  if (!out) {
+    cudaGraphDestroy(graph);
+    return fail(ctx, TC_ERR_INVALID_ARG, "out is NULL");
+  }
+  size_t nodes = 0;
+  e = cudaGraphGetNodes(graph, nullptr, &nodes);
+  std::vector<cudaGraphNode_t> list(nodes);
+  if (e == cudaSuccess && nodes) e = cudaGraphGetNodes(graph, list.data(), &nodes);
+  int64_t kernels = 0;
+  for (size_t i = 0; e == cudaSuccess && i < nodes; ++i) {
+    cudaGraphNodeType t;
+    e = cudaGraphNodeGetType(list[i], &t);
+    if (e == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return cuda_fail(ctx, e, "instantiate capture");
+  }
+  tc_exec* x = new tc_exec;
+  x->device = ctx->device;
+  x->graph = graph;
+  x->exec = exec;
+  x->kernels = kernels;
+  *out = x;
+  return TC_OK;
+}
+
+tc_status tc_exec_launch(tc_exec* x, tc_stream stream) {
+  if (!x) return TC_ERR_INVALID_ARG;
+  if (cudaSetDevice(x->device) != cudaSuccess) return TC_ERR_CUDA;
+  return cudaGraphLaunch(x->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+int64_t tc_exec_kernels(const tc_exec* x) { return x ? x->kernels : 0; }
+
+void tc_exec_destroy(tc_exec* x) {
+  if (!x) return;
+  cudaSetDevice(x->device);
+  if (x->exec) cudaGraphExecDestroy(x->exec);
+  if (x->graph) cudaGraphDestroy(x->graph);
+  delete x;
 }
 
 }  // extern "C"

@@ -40,13 +40,15 @@ namespace tc {
 
 namespace {
 
-constexpr int kTile = 512;           // ids staged per warp; longer lists go to the block kernel
+constexpr int kTile = 256;           // ids staged per warp; longer lists go to the block kernel
 constexpr int kTileWarps = 4;        // warps per block, tile kernel
-constexpr int kTileBitsLog2 = 14;    // filter bits per tile (2 KB): <= 512 / 16384 false positives
-constexpr int kUnroll = 4;           // candidate windows in flight per lane
+constexpr int kTileBitsLog2 = 13;    // filter bits per tile (1 KB): <= 256 / 8192 false positives
+constexpr int kUnroll = 4;           // candidate windows in flight per lane, block kernel
 constexpr int kShortLen = 32;        // N_u shorter than this is walked end to end with others
 constexpr int kOwnCap = 32 * kShortLen;
+constexpr int kTileUnroll = 8;       // candidate windows in flight per lane, tile kernel
 constexpr int kBlockWarps = 8;       // warps per block, block kernel
+constexpr int kHubMinDefault = 64;   // default hub_min: lists of at least this many ids take their in-edges
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
 
@@ -144,15 +146,30 @@ struct BatchSmem {
 
 // Fills the batch record for this lane's edge; *tot is the flattened length of
 // the short lists, *is_short whether this lane's list is one of them, *len its length.
+//
+// Hub side (hub_mode != 0): an edge (v, u) whose N_u has at least a.hub_min ids
+// and more than N_v's dv is left to the hub kernel, which hashes N_u once for
+// all such edges of u and walks the shorter N_v instead; hub_mode 2 also
+// records the edge (per-hub count, flag on the apex vapex).
 __device__ __forceinline__ void batch_setup(BatchSmem& bs, const CountArgs& a, const CountWs& ws, int32_t u,
                                             bool act, int64_t eg, int32_t salt, int32_t lo, int32_t vlen,
                                             int& tot, bool& is_short, int32_t& len, uint32_t* err, bool list_write,
-                                            uint32_t erun0 = 0) {
+                                            uint32_t erun0, int32_t vapex, int32_t dv, int hub_mode) {
   const int lane = lane_id();
   int64_t ub = 0;
   len = 0;
   // the listing write pass walks only edges that have triangles
   if (act && (!list_write || ws.ecount[eg] > 0)) len = list_bounds(a, u, ub, err);
+  if (hub_mode && len >= a.hub_min && len > dv) {
+    const int32_t h = ws.hub_idx[u];
+    if (h >= 0) {
+      if (hub_mode == 2) {
+        atomicAdd(&ws.hub_cnt[h], 1);
+        ws.rev_flag[vapex] = 1;
+      }
+      len = 0;
+    }
+  }
   is_short = len < kShortLen;
   const int32_t slen = is_short ? len : 0;
   const int32_t incl = warp_incl_scan(slen);
@@ -186,8 +203,11 @@ __device__ __forceinline__ unsigned run_mask(int key) {
 
 // Listing: write this lane's triple (if f) at its edge's offset plus the
 // edge's running count; lanes of one edge are contiguous and in candidate order.
+// On the hub side the walked list is N_v of the lane's v and the hashed one N_u
+// of the block's u = `v` here: the triple is (lane's vertex, v, w).
 __device__ __forceinline__ void write_triples(BatchSmem& bs, bool has, bool f, int s, int32_t v, int32_t w,
-                                             const CountArgs& a, const CountWs& ws, uint32_t* err) {
+                                             const CountArgs& a, const CountWs& ws, uint32_t* err,
+                                             bool hub_side = false) {
   const int lane = lane_id();
   const unsigned fm = __ballot_sync(FULL, f);
   if (!fm) return;
@@ -195,8 +215,8 @@ __device__ __forceinline__ void write_triples(BatchSmem& bs, bool has, bool f, i
   if (f) {
     const int64_t idx = bs.ebase[s] + bs.erun[s] + __popc(fm & same & lanemask_lt());
     if (idx < a.cap) {
-      a.tri[3 * idx] = v;
-      a.tri[3 * idx + 1] = bs.u[s];
+      a.tri[3 * idx] = hub_side ? bs.u[s] : v;
+      a.tri[3 * idx + 1] = hub_side ? v : bs.u[s];
       a.tri[3 * idx + 2] = w;
     } else {
       set_err(err, ERR_CAPACITY);
@@ -280,13 +300,14 @@ __device__ __forceinline__ uint32_t tile_batch(TileSmem& sm, int top, int32_t u,
   int tot;
   bool is_short;
   int32_t len;
-  batch_setup(bs, a, ws, u, act, eg, vl, lo, vlen, tot, is_short, len, err, MODE == MODE_LIST_WRITE);
+  batch_setup(bs, a, ws, u, act, eg, vl, lo, vlen, tot, is_short, len, err, MODE == MODE_LIST_WRITE, 0u,
+              vbase + vl, vlen, a.hub_min > 0 ? 2 : 0);
   int qn = 0;
-  for (int32_t p0 = 0; p0 < tot; p0 += 32 * kUnroll) {
-    int32_t w[kUnroll];
-    int s[kUnroll];
+  for (int32_t p0 = 0; p0 < tot; p0 += 32 * kTileUnroll) {
+    int32_t w[kTileUnroll];
+    int s[kTileUnroll];
 #pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
+    for (int k = 0; k < kTileUnroll; ++k) {
       const int32_t p = p0 + 32 * k + lane;
       s[k] = 0;
       w[k] = 0;
@@ -296,7 +317,7 @@ __device__ __forceinline__ uint32_t tile_batch(TileSmem& sm, int top, int32_t u,
       }
     }
 #pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
+    for (int k = 0; k < kTileUnroll; ++k) {
       const int32_t p = p0 + 32 * k + lane;
       const bool pass = p < tot && ftest<kTileBitsLog2>(sm.bits, w[k], bs.salt[s[k]]);
       push<MODE>(sm, pass, w[k], s[k], qn, top, vbase, a, ws, err);
@@ -309,15 +330,15 @@ __device__ __forceinline__ uint32_t tile_batch(TileSmem& sm, int top, int32_t u,
     const int64_t b = bs.beg[e];
     const int32_t le = __shfl_sync(FULL, len, e);
     const int32_t se = bs.salt[e];
-    for (int32_t p0 = 0; p0 < le; p0 += 32 * kUnroll) {
-      int32_t w[kUnroll];
+    for (int32_t p0 = 0; p0 < le; p0 += 32 * kTileUnroll) {
+      int32_t w[kTileUnroll];
 #pragma unroll
-      for (int k = 0; k < kUnroll; ++k) {
+      for (int k = 0; k < kTileUnroll; ++k) {
         const int32_t p = p0 + 32 * k + lane;
         w[k] = p < le ? a.cols[b + p] : 0;
       }
 #pragma unroll
-      for (int k = 0; k < kUnroll; ++k) {
+      for (int k = 0; k < kTileUnroll; ++k) {
         const int32_t p = p0 + 32 * k + lane;
         const bool pass = p < le && ftest<kTileBitsLog2>(sm.bits, w[k], se);
         push<MODE>(sm, pass, w[k], e, qn, top, vbase, a, ws, err);
@@ -347,7 +368,7 @@ __device__ __forceinline__ void add_graph_totals(const CountArgs& a, bool in_gro
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kTileWarps * 32) k_count_tile(CountArgs a, CountWs ws, uint32_t* err) {
+__global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, CountWs ws, uint32_t* err) {
   __shared__ TileSmem s_t[kTileWarps];
   __shared__ unsigned long long s_sum[kTileWarps];
   const int lane = lane_id(), wid = threadIdx.x >> 5;
@@ -502,7 +523,7 @@ __device__ __forceinline__ void hash_insert(int32_t* tab, int32_t w) {
   }
 }
 
-template <int MODE>
+template <int MODE, bool HUB>
 __device__ __forceinline__ void hash_record(BatchSmem& bs, uint32_t* slot_cnt, bool has, int slot, int32_t w, int s,
                                             int32_t v, const CountArgs& a, const CountWs& ws, uint32_t* err) {
   const bool found = slot >= 0;
@@ -510,16 +531,18 @@ __device__ __forceinline__ void hash_record(BatchSmem& bs, uint32_t* slot_cnt, b
     atomicAdd(&bs.cnt[s], 1u);
     if (MODE == MODE_LOCAL) atomicAdd(&slot_cnt[slot], 1u);
   }
-  if (MODE == MODE_LIST_WRITE) write_triples(bs, has, found, s, v, w, a, ws, err);
+  if (MODE == MODE_LIST_WRITE) write_triples(bs, has, found, s, v, w, a, ws, err, HUB);
 }
 
-// One batch of edges (v, u), u on this lane if `act`, against the hashed chunk
-// of N_v whose ids lie in [lo, hi].  Returns the matches of this lane's edge.
-template <int MODE>
+// One batch of edges against the hashed chunk (ids in [lo, hi]) of the block
+// vertex v's list: block kernel, edges (v, u) with u on this lane if `act`,
+// walking N_u; hub kernel (HUB), edges (x, v) with x on this lane, walking N_x.
+// eg is the lane's edge (its position in cols).  Returns the lane's matches.
+template <int MODE, bool HUB>
 __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab, uint32_t* slot_cnt, int32_t lo,
                                                int32_t hi, int32_t u, bool act, int64_t eg, int32_t v,
                                                const CountArgs& a, const CountWs& ws, uint32_t* err,
-                                               bool chunked, bool first_chunk) {
+                                               bool chunked, bool first_chunk, int32_t dv) {
   constexpr int L = HashCfg<MODE>::kLog2;
   const int lane = lane_id();
   int tot;
@@ -527,7 +550,10 @@ __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab
   int32_t len;
   // listing a vertex hashed in several chunks: an edge's triples continue where the last chunk stopped
   const uint32_t erun0 = (MODE == MODE_LIST_WRITE && chunked && !first_chunk && act) ? ws.erun[eg] : 0u;
-  batch_setup(bs, a, ws, u, act, eg, 0, 0, 0, tot, is_short, len, err, MODE == MODE_LIST_WRITE, erun0);
+  // block kernel: edges bound for the hub side are recorded once, with the first chunk
+  const int hub_mode = (HUB || a.hub_min <= 0) ? 0 : (first_chunk ? 2 : 1);
+  batch_setup(bs, a, ws, u, act, eg, 0, 0, 0, tot, is_short, len, err, MODE == MODE_LIST_WRITE, erun0, v, dv,
+              hub_mode);
   for (int32_t p0 = 0; p0 < tot; p0 += 32 * kUnroll) {
     int32_t w[kUnroll];
     int s[kUnroll];
@@ -545,7 +571,7 @@ __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab
     for (int k = 0; k < kUnroll; ++k) {
       const int32_t p = p0 + 32 * k + lane;
       const int slot = (w[k] >= lo && w[k] <= hi) ? hash_find<L>(tab, w[k]) : -1;
-      hash_record<MODE>(bs, slot_cnt, p < tot, slot, w[k], s[k], v, a, ws, err);
+      hash_record<MODE, HUB>(bs, slot_cnt, p < tot, slot, w[k], s[k], v, a, ws, err);
     }
   }
   unsigned lm = __ballot_sync(FULL, len > 0 && !is_short);
@@ -565,7 +591,7 @@ __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab
       for (int k = 0; k < kUnroll; ++k) {
         const int32_t p = p0 + 32 * k + lane;
         const int slot = (w[k] >= lo && w[k] <= hi) ? hash_find<L>(tab, w[k]) : -1;
-        hash_record<MODE>(bs, slot_cnt, p < le, slot, w[k], e, v, a, ws, err);
+        hash_record<MODE, HUB>(bs, slot_cnt, p < le, slot, w[k], e, v, a, ws, err);
       }
     }
   }
@@ -574,7 +600,12 @@ __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab
   return act ? bs.cnt[lane] : 0u;
 }
 
-template <int MODE>
+// Block kernel (HUB = false): one block per queued apex v with a long N_v.
+// Hub kernel (HUB = true): one block per work item (hub u, segment of the
+// edges (x, u) recorded for u's side); N_u is hashed and each N_x walked.
+// Both: the block vertex's list is hashed in chunks of H::kCap ids; the
+// lane's vertex gets its edge's matches, the block vertex their sum.
+template <int MODE, bool HUB>
 __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a, CountWs ws, uint32_t* err) {
   using H = HashCfg<MODE>;
   extern __shared__ int32_t tab[];
@@ -583,11 +614,22 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
   __shared__ unsigned long long s_red[kBlockWarps];
   const int lane = lane_id(), wid = threadIdx.x >> 5;
   unsigned long long acc = 0;
-  const uint32_t qn = ws.counters[0];
+  const uint32_t qn = HUB ? static_cast<uint32_t>(min64(ws.counters[kCtrItems], ws.items_cap))
+                         : ws.counters[kCtrBigQueue];
   for (uint32_t qi = blockIdx.x; qi < qn; qi += gridDim.x) {
-    const int32_t v = ws.big_queue[qi];
+    int32_t v;
+    int64_t ent_lo = 0, ent_n = 0;  // hub kernel: this item's edges in hub_ent
+    if (HUB) {
+      const int2 it = ws.hub_items[qi];
+      v = ws.hubs[it.x];
+      ent_lo = ws.hub_off[it.x] + static_cast<int64_t>(it.y) * kHubSeg;
+      ent_n = max64(0, min64(min64(kHubSeg, ws.hub_off[it.x + 1] - ent_lo), a.m - ent_lo));
+    } else {
+      v = ws.big_queue[qi];
+    }
     const int64_t b = a.offsets[v], e = a.offsets[v + 1];
     const int64_t dv = e - b;
+    const int64_t nl = HUB ? ent_n : dv;  // lists walked against v's
     unsigned long long cv = 0;
     for (int64_t c0 = 0; c0 < dv; c0 += H::kCap) {
       const int clen = static_cast<int>(min64(H::kCap, dv - c0));
@@ -607,24 +649,42 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
         if (threadIdx.x == 0) set_err(err, ERR_BAD_ID);
         break;
       }
-      // the chunk is a sorted run of N_v: its ids lie in [lo, hi]
+      // the chunk is a sorted run of the block vertex's list: its ids lie in [lo, hi]
       const int32_t lo = a.cols[b + c0], hi = a.cols[b + c0 + clen - 1];
-      for (int64_t ub = static_cast<int64_t>(wid) * 32; ub < dv; ub += kBlockWarps * 32) {
-        const int nb = static_cast<int>(min64(32, dv - ub));
-        const bool act = lane < nb;
-        const int32_t u = act ? a.cols[b + ub + lane] : 0;
-        const uint32_t c = hash_batch<MODE>(s_b[wid], tab, slot_cnt, lo, hi, u, act, b + ub + lane, v, a, ws, err,
-                                            dv > H::kCap, c0 == 0);
+      for (int64_t ub = static_cast<int64_t>(wid) * 32; ub < nl; ub += kBlockWarps * 32) {
+        const int nb = static_cast<int>(min64(32, nl - ub));
+        bool act = lane < nb;
+        int32_t x = 0;
+        int64_t eg = 0;
+        if (act) {
+          if (HUB) {  // edge (x, v): v sits at position en.y of N_x
+            const int2 en = ws.hub_ent[ent_lo + ub + lane];
+            x = en.x;
+            if (static_cast<uint32_t>(x) < static_cast<uint32_t>(a.n) && en.y >= 0 &&
+                a.offsets[x] + en.y < a.offsets[x + 1]) {
+              eg = a.offsets[x] + en.y;
+            } else {  // an entry the fill pass did not write: skip it, report the mismatch
+              set_err(err, ERR_BAD_CSR);
+              x = 0;
+              act = false;
+            }
+          } else {
+            x = a.cols[b + ub + lane];
+            eg = b + ub + lane;
+          }
+        }
+        const uint32_t c = hash_batch<MODE, HUB>(s_b[wid], tab, slot_cnt, lo, hi, x, act, eg, v, a, ws, err,
+                                                 dv > H::kCap, c0 == 0, static_cast<int32_t>(dv));
         cv += c;
         if (act && (MODE == MODE_LOCAL || MODE == MODE_LIST_COUNT) && ws.ecount) {
           // the same lane holds the same edge in every chunk
-          if (c0 == 0) ws.ecount[b + ub + lane] = static_cast<int32_t>(c);
-          else ws.ecount[b + ub + lane] += static_cast<int32_t>(c);
+          if (c0 == 0) ws.ecount[eg] = static_cast<int32_t>(c);
+          else ws.ecount[eg] += static_cast<int32_t>(c);
         }
         if (MODE == MODE_LOCAL && c)
-          atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + u), static_cast<unsigned long long>(c));
+          atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + x), static_cast<unsigned long long>(c));
       }
-      if (MODE == MODE_LOCAL) {  // T_w once per (v, w) of this chunk
+      if (MODE == MODE_LOCAL) {  // T_w once per (block vertex, w) of this chunk
         __syncthreads();
         for (int i = threadIdx.x; i < H::kSlots; i += blockDim.x)
           if (slot_cnt[i])
@@ -647,6 +707,93 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
   if (threadIdx.x == 0 && acc && a.total) atomicAdd(a.total, acc);
 }
 
+// ---------------------------------------------------------------------------
+// Hub side preparation.  Hubs are the vertices with |N_u| >= hub_min; the
+// tile and block kernels count, per hub, the edges they leave to its side
+// (batch_setup) and flag their apex vertices; the flagged vertices' lists are
+// then walked again to place each such edge in its hub's segment of hub_ent.
+// ---------------------------------------------------------------------------
+
+__global__ void k_hub_list(int32_t n, const int64_t* __restrict__ offsets, int32_t hub_min, CountWs ws) {
+  const int lane = lane_id();
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; i0 < n; i0 += stride) {
+    const int64_t u = i0 + threadIdx.x;
+    bool hub = false;
+    if (u < n) {
+      const int64_t d = offsets[u + 1] - offsets[u];
+      hub = d >= hub_min;
+      ws.rev_flag[u] = 0;
+      if (!hub) ws.hub_idx[u] = -1;
+    }
+    const unsigned hm = __ballot_sync(FULL, hub);
+    if (hm) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(&ws.counters[kCtrHubs], static_cast<uint32_t>(__popc(hm)));
+      base = __shfl_sync(FULL, base, 0);
+      if (hub) {
+        const int32_t h = static_cast<int32_t>(base + __popc(hm & lanemask_lt()));
+        ws.hub_idx[u] = h;
+        ws.hubs[h] = static_cast<int32_t>(u);
+        ws.hub_cnt[h] = 0;
+        ws.hub_fill[h] = 0;
+      }
+    }
+  }
+}
+
+// Walks the lists of the flagged apex vertices (a warp per vertex) and places
+// every edge (v, u) that batch_setup left to u's side -- the same test, on
+// the same lengths -- at hub_off[h] + (a fill cursor of hub h).
+template <int MODE>
+__global__ void k_hub_fill(CountArgs a, CountWs ws, uint32_t* err) {
+  const int lane = lane_id();
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  const int64_t w0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  for (int64_t base = w0 * 32; base < a.n; base += warps * 32) {
+    const int64_t vl = base + lane;
+    const bool flagged = vl < a.n && ws.rev_flag[vl];
+    unsigned fm = __ballot_sync(FULL, flagged);
+    while (fm) {
+      const int32_t v = static_cast<int32_t>(base + __ffs(fm) - 1);
+      fm &= fm - 1;
+      const int64_t b = a.offsets[v], dv = a.offsets[v + 1] - b;
+      if (b < 0 || dv < 0 || b + dv > a.m) {
+        if (lane == 0) set_err(err, ERR_BAD_CSR);
+        continue;
+      }
+      for (int64_t p = lane; p < dv; p += 32) {
+        if (MODE == MODE_LIST_WRITE && ws.ecount[b + p] <= 0) continue;
+        const int32_t u = a.cols[b + p];
+        int64_t ub;
+        const int32_t len = list_bounds(a, u, ub, err);
+        if (len < a.hub_min || len <= dv) continue;
+        const int32_t h = ws.hub_idx[u];
+        if (h < 0) continue;
+        const int32_t pos = atomicAdd(&ws.hub_fill[h], 1);
+        const int64_t at = ws.hub_off[h] + pos;
+        if (pos < ws.hub_cnt[h] && at < a.m) ws.hub_ent[at] = make_int2(v, static_cast<int32_t>(p));
+        else set_err(err, ERR_BAD_CSR);  // the two walks disagree: the CSR changed underneath
+      }
+    }
+  }
+}
+
+// One work item per kHubSeg edges of each hub.
+__global__ void k_hub_items(CountWs ws) {
+  const int64_t cap = ws.items_cap;
+  const uint32_t hubs = ws.counters[kCtrHubs];
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t h = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; h < hubs; h += stride) {
+    const int32_t c = ws.hub_cnt[h];
+    const int32_t segs = (c + kHubSeg - 1) / kHubSeg;
+    if (!segs) continue;
+    const uint32_t at = atomicAdd(&ws.counters[kCtrItems], static_cast<uint32_t>(segs));
+    for (int32_t j = 0; j < segs; ++j)
+      if (at + j < cap) ws.hub_items[at + j] = make_int2(static_cast<int32_t>(h), j);
+  }
+}
+
 __global__ void k_clustering(int32_t n, const int32_t* __restrict__ deg, const int64_t* __restrict__ tv,
                              double* __restrict__ cc) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -659,12 +806,34 @@ __global__ void k_clustering(int32_t n, const int32_t* __restrict__ deg, const i
   }
 }
 
+// Dynamic shared memory of k_count_block<MODE, HUB> beyond the 48 KB default: opt in once per device.
+template <int MODE, bool HUB>
+cudaError_t block_smem_optin(Ctx* ctx, size_t smem) {
+  static bool attr_set[64] = {false};
+  if (ctx->device >= 0 && ctx->device < 64 && !attr_set[ctx->device]) {
+    const cudaError_t e = cudaFuncSetAttribute(k_count_block<MODE, HUB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    attr_set[ctx->device] = true;
+  }
+  return cudaSuccess;
+}
+
 template <int MODE>
 cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s) {
-  static const char* kNames[4][2] = {{"count.tile", "count.block"},
-                                     {"local.tile", "local.block"},
-                                     {"list_count.tile", "list_count.block"},
-                                     {"list_write.tile", "list_write.block"}};
+  static const char* kNames[4][4] = {
+      {"count.tile", "count.block", "count.hub_prep", "count.hub"},
+      {"local.tile", "local.block", "local.hub_prep", "local.hub"},
+      {"list_count.tile", "list_count.block", "list_count.hub_prep", "list_count.hub"},
+      {"list_write.tile", "list_write.block", "list_write.hub_prep", "list_write.hub"}};
+  const bool hub = a.hub_min > 0;
+  const int n_grid = static_cast<int>(min64((static_cast<int64_t>(a.n) + 255) / 256,
+                                            static_cast<int64_t>(ctx->sm_count) * 8));
+  if (hub) {
+    Stage st(ctx, s, kNames[MODE][2]);
+    k_hub_list<<<n_grid, 256, 0, s>>>(a.n, a.offsets, a.hub_min, ws);
+    counted(ctx);
+  }
   // persistent grids, but no more blocks than there is work for (small graphs leave room for other streams)
   const int tgrid = static_cast<int>(min64(
       persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_tile<MODE>), kTileWarps * 32, 0),
@@ -674,22 +843,35 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
     k_count_tile<MODE><<<tgrid, kTileWarps * 32, 0, s>>>(a, ws, ctx->d_err);
   }
   const size_t smem = HashCfg<MODE>::kBytes;
-  // static plus dynamic shared memory exceeds the 48 KB default: opt in once per device
-  static bool attr_set[64] = {false};
-  if (ctx->device >= 0 && ctx->device < 64 && !attr_set[ctx->device]) {
-    const cudaError_t e = cudaFuncSetAttribute(k_count_block<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    attr_set[ctx->device] = true;
-  }
+  cudaError_t e = block_smem_optin<MODE, false>(ctx, smem);
+  if (e != cudaSuccess) return e;
   const int bgrid = static_cast<int>(min64(
-      persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_block<MODE>), kBlockWarps * 32, smem),
+      persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_block<MODE, false>), kBlockWarps * 32, smem),
       max64(1, a.m / (a.tile_max + 1))));  // at most m / (tile_max + 1) lists go to this kernel
   {
     Stage st(ctx, s, kNames[MODE][1]);
-    k_count_block<MODE><<<bgrid, kBlockWarps * 32, smem, s>>>(a, ws, ctx->d_err);
+    k_count_block<MODE, false><<<bgrid, kBlockWarps * 32, smem, s>>>(a, ws, ctx->d_err);
   }
   counted(ctx, 2);
+  if (hub) {
+    {
+      Stage st(ctx, s, kNames[MODE][2]);
+      // hub_off = scan of the per-hub counts (as many as there are hubs, read on the device)
+      e = exclusive_scan_i32(ws.hub_cnt, ws.hub_off, a.n, ws.hub_scan, s, ws.counters + kCtrHubs);
+      if (e != cudaSuccess) return e;
+      const int fgrid = static_cast<int>(min64((static_cast<int64_t>(a.n) + 255) / 256,
+                                               static_cast<int64_t>(ctx->sm_count) * 16));
+      k_hub_fill<MODE><<<fgrid, 256, 0, s>>>(a, ws, ctx->d_err);
+      k_hub_items<<<n_grid, 256, 0, s>>>(ws);
+      counted(ctx, a.n > 0 ? 5 : 3);
+    }
+    if ((e = block_smem_optin<MODE, true>(ctx, smem)) != cudaSuccess) return e;
+    const int hgrid = persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_block<MODE, true>),
+                                        kBlockWarps * 32, smem);
+    Stage st(ctx, s, kNames[MODE][3]);
+    k_count_block<MODE, true><<<hgrid, kBlockWarps * 32, smem, s>>>(a, ws, ctx->d_err);
+    counted(ctx);
+  }
   return cudaGetLastError();
 }
 
@@ -697,8 +879,19 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
 
 CountWs carve_count(Carver& c, int32_t n, int64_t m, bool listing) {
   CountWs w{};
-  w.big_queue = c.take<int32_t>(static_cast<size_t>(n > 0 ? n : 1));
-  w.counters = c.take<uint32_t>(4);
+  const size_t n1 = static_cast<size_t>(n > 0 ? n : 1), m1 = static_cast<size_t>(m > 0 ? m : 1);
+  w.big_queue = c.take<int32_t>(n1);
+  w.counters = c.take<uint32_t>(kCtrSlots);
+  w.hub_idx = c.take<int32_t>(n1);
+  w.hubs = c.take<int32_t>(n1);
+  w.hub_cnt = c.take<int32_t>(n1);
+  w.hub_fill = c.take<int32_t>(n1);
+  w.hub_off = c.take<int64_t>(n1 + 1);
+  w.rev_flag = c.take<uint8_t>(n1);
+  w.hub_ent = c.take<int2>(m1);
+  w.items_cap = hub_item_cap(n, m);
+  w.hub_items = c.take<int2>(static_cast<size_t>(w.items_cap));
+  w.hub_scan = carve_scan(c, n);
   if (listing) {
     w.ecount = c.take<int32_t>(static_cast<size_t>(m > 0 ? m : 1));
     w.erun = c.take<uint32_t>(static_cast<size_t>(m > 0 ? m : 1));
@@ -718,11 +911,13 @@ int persistent_blocks(Ctx* ctx, const void* kernel, int threads, size_t dyn_smem
 }
 
 cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a_in, CountWs ws, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(ws.counters, 0, sizeof(uint32_t) * 4, s);
+  cudaError_t e = cudaMemsetAsync(ws.counters, 0, sizeof(uint32_t) * kCtrSlots, s);
   if (e != cudaSuccess) return e;
   if (a_in.n <= 0) return cudaGetLastError();
   CountArgs a = a_in;
   a.tile_max = (ctx->tile_max > 0 && ctx->tile_max < kTile) ? ctx->tile_max : kTile;
+  // hub side: needs its workspace (absent in the allocation-free entry point)
+  a.hub_min = (ws.hub_idx && ctx->hub_min >= 0) ? (ctx->hub_min > 0 ? ctx->hub_min : kHubMinDefault) : 0;
   switch (mode) {
     case MODE_COUNT: return launch_mode<MODE_COUNT>(ctx, a, ws, s);
     case MODE_LOCAL: return launch_mode<MODE_LOCAL>(ctx, a, ws, s);

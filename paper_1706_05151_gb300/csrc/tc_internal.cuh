@@ -56,6 +56,10 @@ struct Ctx {
   int64_t launches = 0;       // kernels this context has launched
   int32_t tile_max = 0;       // tuning: longest N_v counted by the tile kernel (0 = its capacity)
   int32_t grid_div = 1;       // tuning: persistent grids use 1/grid_div of the resident capacity
+  int32_t hub_min = 0;        // tuning: hub side for |N_u| >= hub_min (0: default, -1: off)
+  int capturing = 0;          // inside tc_capture_begin .. tc_capture_end
+  int saved_async = 0;        // async flag before the capture
+  int capture_status = 0;     // first failure inside the capture (0 = none)
   Profiler prof;
   char last_error[256] = {0};
 };
@@ -101,14 +105,37 @@ constexpr int64_t kScanTile = kScanThreads * kScanItems;
 inline int64_t scan_tiles(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
 inline ScanWs carve_scan(Carver& c, int64_t n) { return ScanWs{c.take<int64_t>(scan_tiles(n) + 2)}; }
 
+// Counter slots of CountWs::counters.
+enum CountCounter : int {
+  kCtrBigQueue = 0,  // vertices queued for the block kernel
+  kCtrCursor = 1,    // vertex cursor of the tile kernel
+  kCtrHubs = 2,      // hub vertices (|N_u| >= hub_min)
+  kCtrItems = 3,     // work items of the hub kernel
+  kCtrSlots = 8
+};
+constexpr int kHubSeg = 1024;  // in-edges of a hub per work item of the hub kernel
+
 struct CountWs {
   int32_t* big_queue;   // vertices left to the block kernel
-  uint32_t* counters;   // [0] queue length, [1] vertex cursor of the tile kernel, [2..3] spare
+  uint32_t* counters;   // kCtrSlots counters (CountCounter)
   int32_t* ecount;      // listing: triangles per oriented edge (m)
   uint32_t* erun;       // listing: triples written per edge, carried across hash chunks (m)
   int64_t* eoff;        // listing: output offset per oriented edge (m + 1; eoff[m] = T)
   ScanWs scan;          // listing: scan over the m edge counts
+  // hub side: edges (v, u) with |N_u| >= hub_min and |N_u| > |N_v| are counted
+  // from u's side (NULL hub_idx: off)
+  int32_t* hub_idx;     // per vertex: its index among the hubs, or -1 (n)
+  int32_t* hubs;        // hub vertex of each index (n)
+  int32_t* hub_cnt;     // edges counted from each hub's side (n)
+  int32_t* hub_fill;    // fill cursor per hub (n)
+  int64_t* hub_off;     // exclusive scan of hub_cnt (n + 1)
+  uint8_t* rev_flag;    // per vertex v: some edge (v, u) goes to u's side (n)
+  int2* hub_ent;        // per hub, its edges as (v, position of u in N_v) (m)
+  int2* hub_items;      // work items (hub index, segment of kHubSeg edges) ...
+  int64_t items_cap;    // ... room for this many
+  ScanWs hub_scan;      // scan over hub_cnt
 };
+inline int64_t hub_item_cap(int32_t n, int64_t m) { return static_cast<int64_t>(n) + m / kHubSeg + 1; }
 CountWs carve_count(Carver& c, int32_t n, int64_t m, bool listing);
 
 struct OrientWs {
@@ -142,7 +169,9 @@ cudaError_t launch_batch_prepare(Ctx* ctx, int32_t G, int32_t N, int64_t E, cons
 
 // ---- launchers (stream-ordered, no synchronisation) -------------------------
 
-cudaError_t exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, ScanWs ws, cudaStream_t s);
+// With n_dev, the scan covers min(n, *n_dev) entries (a length a kernel earlier in the stream wrote).
+cudaError_t exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, ScanWs ws, cudaStream_t s,
+                               const uint32_t* n_dev = nullptr);
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, ScanWs ws, cudaStream_t s);
 
 cudaError_t launch_orient(Ctx* ctx, int32_t n, int64_t m, const int32_t* edges, int64_t* offsets,
@@ -162,6 +191,7 @@ struct CountArgs {
   unsigned long long* graph_total = nullptr;  // batched form: T per graph ...
   const int32_t* gid = nullptr;               // ... indexed by the graph id of the apex vertex
   int32_t tile_max = 0;                       // lists longer than this go to the block kernel (set by launch_count)
+  int32_t hub_min = 0;                        // hub side for lists of at least this length (0: off; set by launch_count)
 };
 cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a, CountWs ws, cudaStream_t s);
 // Listing: eoff = exclusive scan of ecount (after a MODE_LIST_COUNT or MODE_LOCAL pass).

@@ -1,4 +1,5 @@
-// Device-wide exclusive prefix sum: out[i] = in[0] + ... + in[i-1], out[n] = total.
+// Device-wide exclusive prefix sum: out[i] = in[0] + ... + in[i-1], out[n] = total
+// (n the host length, or the smaller length found at *n_dev when the stream reaches the scan).
 // Used for CSR offsets (Figure 2 preprocessing builds N_v contiguously) and for
 // the listing and sparsification output positions.  Three stream-ordered
 // launches: per-tile sums, one block scanning the tile sums, per-tile rescan.
@@ -42,12 +43,22 @@ __device__ __forceinline__ int64_t block_exclusive(int64_t x, int64_t* warp_sums
   return r;
 }
 
+// Scan length: the host bound n, or the smaller length a kernel earlier in the stream left at *n_dev.
+__device__ __forceinline__ int64_t scan_len(int64_t n, const uint32_t* n_dev) {
+  return n_dev ? min64(n, static_cast<int64_t>(*n_dev)) : n;
+}
+
 template <class T>
-__global__ void __launch_bounds__(kScanThreads) k_tile_sums(const T* __restrict__ in, int64_t n,
-                                                            int64_t* __restrict__ sums) {
+__global__ void __launch_bounds__(kScanThreads) k_tile_sums(const T* __restrict__ in, int64_t n_max,
+                                                            const uint32_t* n_dev, int64_t* __restrict__ sums) {
   __shared__ int64_t warp_sums[32];
   __shared__ int64_t total;
+  const int64_t n = scan_len(n_max, n_dev);
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile;
+  if (base >= n && base > 0) {  // past a device-side length: this tile sums to zero
+    if (threadIdx.x == 0) sums[blockIdx.x] = 0;
+    return;
+  }
   int64_t s = 0;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) s += load_or_zero(in, base + k * kScanThreads + threadIdx.x, n);
@@ -75,13 +86,16 @@ __global__ void __launch_bounds__(1024) k_scan_sums(int64_t* sums, int64_t tiles
 __device__ __forceinline__ int pad(int i) { return i + i / kScanItems; }
 
 template <class T>
-__global__ void __launch_bounds__(kScanThreads) k_tile_scan(const T* __restrict__ in, int64_t n,
-                                                            const int64_t* __restrict__ sums,
+__global__ void __launch_bounds__(kScanThreads) k_tile_scan(const T* __restrict__ in, int64_t n_max,
+                                                            const uint32_t* n_dev, const int64_t* __restrict__ sums,
                                                             int64_t* __restrict__ out, int64_t tiles) {
   __shared__ int64_t tile[kScanTile + kScanTile / kScanItems];
   __shared__ int64_t warp_sums[32];
   __shared__ int64_t total;
+  const int64_t n = scan_len(n_max, n_dev);
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile;
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = sums[tiles];
+  if (base >= n) return;
   // coalesced load into shared memory, then each thread owns kScanItems consecutive items
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
@@ -105,32 +119,32 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const T* __restrict_
     int64_t i = base + k * kScanThreads + threadIdx.x;
     if (i < n) out[i] = tile[pad(k * kScanThreads + threadIdx.x)];
   }
-  if (blockIdx.x == tiles - 1 && threadIdx.x == 0) out[n] = sums[tiles];
 }
 
 __global__ void k_write_zero(int64_t* out) { out[0] = 0; }
 
 template <class T>
-cudaError_t scan_impl(const T* in, int64_t* out, int64_t n, ScanWs ws, cudaStream_t s) {
+cudaError_t scan_impl(const T* in, int64_t* out, int64_t n, const uint32_t* n_dev, ScanWs ws, cudaStream_t s) {
   if (n <= 0) {
     k_write_zero<<<1, 1, 0, s>>>(out);
     return cudaGetLastError();
   }
   const int64_t tiles = scan_tiles(n);
-  k_tile_sums<T><<<static_cast<unsigned>(tiles), kScanThreads, 0, s>>>(in, n, ws.block_sums);
+  k_tile_sums<T><<<static_cast<unsigned>(tiles), kScanThreads, 0, s>>>(in, n, n_dev, ws.block_sums);
   k_scan_sums<<<1, 1024, 0, s>>>(ws.block_sums, tiles);
-  k_tile_scan<T><<<static_cast<unsigned>(tiles), kScanThreads, 0, s>>>(in, n, ws.block_sums, out, tiles);
+  k_tile_scan<T><<<static_cast<unsigned>(tiles), kScanThreads, 0, s>>>(in, n, n_dev, ws.block_sums, out, tiles);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, ScanWs ws, cudaStream_t s) {
-  return scan_impl<int32_t>(in, out, n, ws, s);
+cudaError_t exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, ScanWs ws, cudaStream_t s,
+                               const uint32_t* n_dev) {
+  return scan_impl<int32_t>(in, out, n, n_dev, ws, s);
 }
 
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, ScanWs ws, cudaStream_t s) {
-  return scan_impl<int64_t>(in, out, n, ws, s);
+  return scan_impl<int64_t>(in, out, n, nullptr, ws, s);
 }
 
 }  // namespace tc

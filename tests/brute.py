@@ -6,6 +6,7 @@ orientation or intersection, so they pin the oracle from outside.
 from __future__ import annotations
 
 import itertools
+import math
 
 import numpy as np
 
@@ -78,3 +79,24 @@ def canon(tri) -> np.ndarray:
         return t
     order = np.lexsort((t[:, 2], t[:, 1], t[:, 0]))
     return t[order]
+
+
+def clique_with_pendants(k: int, a: int, width: int = 4):
+    """K_k plus k*a/width pendant vertices, pendant j joined to clique vertices
+    width*j .. width*j + width - 1 (mod k): every clique vertex gets exactly `a`
+    pendants, so clique degrees stay equal and the order of Eq. (1) among them
+    is by id -- clique vertex 0 has the longest list (k - 1 ids) and every
+    pendant (degree width) precedes it.  Closed forms: T = C(k,3) + P*C(width,2);
+    T_v = C(k-1,2) + (width-1)*a on the clique, C(width,2) on a pendant."""
+    assert (k * a) % width == 0
+    P = k * a // width
+    clique = np.array([(i, j) for i in range(k) for j in range(i + 1, k)], dtype=np.int32)
+    pend = np.empty((P * width, 2), dtype=np.int32)
+    j = np.repeat(np.arange(P), width)
+    pend[:, 0] = (width * j + np.tile(np.arange(width), P)) % k
+    pend[:, 1] = k + j
+    e = np.concatenate([clique, pend])
+    T = math.comb(k, 3) + P * math.comb(width, 2)
+    tv = np.concatenate([np.full(k, math.comb(k - 1, 2) + (width - 1) * a, np.int64),
+                         np.full(P, math.comb(width, 2), np.int64)])
+    return k + P, e, T, tv

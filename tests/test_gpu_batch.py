@@ -80,3 +80,67 @@ def test_batch_rejects_bad_local_ids(tc):
     with pytest.raises(tc.TcError) as ex:
         tc.batch(b)
     assert ex.value.status == 2
+
+
+def test_captured_batch_replays_match_plain_calls(tc):
+    """tc_capture_begin/end around tc_batch: each replay equals a plain tc_batch on
+    the buffers' current contents, including after the inputs are refilled in place."""
+    graphs = mixed_graphs()
+    b = tc.make_batch([(n, synth.shuffle_edges(e, i)) for i, (n, e) in enumerate(graphs)], "cuda")
+    want_T, want_tv, _ = tc.batch(b)
+    want_T, want_tv = want_T.clone(), want_tv.clone()
+    cap = tc.CapturedBatch(b, local=True)
+    assert cap.kernels > 0
+    for _ in range(2):
+        cap.totals.fill_(-1)
+        cap.replay()
+        torch.cuda.synchronize()
+        T, tv, union = cap.result()
+        assert torch.equal(T, want_T)
+        assert torch.equal(tv, want_tv)
+    tc.default_context().status()  # no device-side input error in the replays
+    # refill in place: every graph relabelled by a random permutation of its own ids
+    vbase = b.vbase.cpu().numpy()
+    perm_edges = []
+    perms = []
+    for g, (n, e) in enumerate(graphs):
+        p = np.random.default_rng(g).permutation(n).astype(np.int32) if n else np.zeros(0, np.int32)
+        perms.append(p)
+        perm_edges.append(synth.shuffle_edges(synth.relabel(e, p), 100 + g) if len(e) else e)
+    b.edges.copy_(torch.from_numpy(np.concatenate([np.asarray(e, np.int32).reshape(-1, 2) for e in perm_edges])))
+    cap.replay()
+    torch.cuda.synchronize()
+    T, tv, _ = cap.result()
+    assert torch.equal(T, want_T)
+    tv = tv.cpu().numpy()
+    wtv = want_tv.cpu().numpy()
+    for g, (n, _) in enumerate(graphs):
+        if n:
+            # vertex x of the original graph is vertex perms[g][x] of the relabelled one
+            assert np.array_equal(tv[vbase[g] + perms[g]], wtv[vbase[g]:vbase[g + 1]]), g
+    # a plain call on the refilled buffers agrees with the replay
+    T2, tv2, _ = tc.batch(b)
+    assert torch.equal(T2, cap.totals)
+    assert np.array_equal(tv2.cpu().numpy(), tv)
+    cap.close()
+
+
+def test_capture_refuses_synchronizing_calls(tc):
+    INVALID_ARG = 1
+    ctx = tc.Context(0)
+    g = tc.orient(torch.from_numpy(synth.complete(10)).cuda(), 10, ctx)
+    s = torch.cuda.Stream()
+    lib = ctx.lib
+    sp = tc.ctypes.c_void_p(s.cuda_stream)
+    assert lib.tc_capture_begin(ctx.handle, sp) == 0
+    cnt = tc.ctypes.c_int64()
+    ws = ctx.workspace(tc.TC_OP_LIST, g.n, g.m)
+    st = lib.tc_list(ctx.handle, tc.ctypes.byref(g.struct()), None, 0, tc.ctypes.byref(cnt), tc._ptr(ws),
+                     ws.numel(), sp)
+    assert st == INVALID_ARG
+    x = tc.ctypes.c_void_p()
+    # the refused call spoils the capture: end reports it and returns no sequence
+    assert lib.tc_capture_end(ctx.handle, sp, tc.ctypes.byref(x)) == INVALID_ARG
+    # the context works normally afterwards
+    assert tc.count(g, ctx) == 120
+    ctx.close()

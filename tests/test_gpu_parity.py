@@ -297,13 +297,15 @@ def test_autotuner_records_a_candidate(tc, tmp_path):
     g = tc.orient(to_dev(synth.rmat(13, 16, 42)), n)
     path = str(tmp_path / "tuning.json")
     try:
-        best, times = autotune.tune(g, repeats=1, path=path)
+        best, times, hub, hub_times = autotune.tune(g, repeats=1, path=path)
         assert best in autotune.CANDIDATES and set(times) == set(autotune.CANDIDATES)
-        assert autotune.apply(g, path=path) == best
+        assert hub in autotune.HUB_CANDIDATES and set(hub_times) == set(autotune.HUB_CANDIDATES)
+        assert autotune.apply(g, path=path) == (best, hub)
         assert autotune.shape_class(g) in autotune.load_table(path)
         assert tc.count(g) == oracle.count(n, synth.rmat(13, 16, 42))["T"]
     finally:
         tc.default_context().set_tuning(0, 1)
+        tc.default_context().set_hub_min(0)
 
 
 def test_listing_of_lists_longer_than_one_hash_chunk(tc):

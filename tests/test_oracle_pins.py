@@ -321,3 +321,17 @@ def test_sparsify_unbiased_with_paper_variance():
     ests = np.array([oracle.sparsify_count(n, e, s, q)[2] for s in range(S)])
     assert abs(ests.mean() - T) < 4.5 * math.sqrt(var / S)
     assert 0.7 * var < ests.var(ddof=1) < 1.4 * var
+
+
+def test_clique_with_pendants_closed_form():
+    """The closed form the GPU hub tests use, checked against the oracle and the definition."""
+    from tests.brute import clique_with_pendants, triangles_by_triples, per_vertex_from_list
+    for k, a, width in ((12, 4, 4), (9, 3, 3), (40, 12, 4)):
+        n, e, T, tv = clique_with_pendants(k, a, width)
+        r = oracle.count(n, e, local=True)
+        assert r["T"] == T
+        assert np.array_equal(r["tv"], tv)
+        if n <= 40:
+            tris = triangles_by_triples(n, e)
+            assert len(tris) == T
+            assert np.array_equal(per_vertex_from_list(n, tris), tv)
