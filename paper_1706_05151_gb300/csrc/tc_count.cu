@@ -139,8 +139,6 @@ struct BatchSmem {
   uint32_t cnt[32];       // matches of the edge
   uint32_t erun[32];      // listing: triples of the edge written so far
   int64_t ebase[32];      // listing: output offset of the edge
-  int32_t qw[64];         // filter survivors: candidate id ...
-  int32_t qs[64];         // ... and its edge
   uint8_t own[kOwnCap];   // flattened position -> edge, short lists
 };
 
@@ -236,6 +234,8 @@ struct TileSmem {
   uint32_t bits[(1 << kTileBitsLog2) / 32];
   int32_t vlo[32];     // tile start of each chunk lane's list (-1 before the group, > S after)
   uint32_t vcnt[32];   // triangles with apex v (chunk lane)
+  int32_t qw[64];      // filter survivors: candidate id ...
+  int32_t qs[64];      // ... and its edge
   BatchSmem bs;
 };
 
@@ -247,8 +247,8 @@ __device__ __forceinline__ void exact_flush(TileSmem& sm, int cnt, int top, int3
   const int lane = lane_id();
   __syncwarp();
   const bool has = lane < cnt;
-  const int s = has ? bs.qs[lane] : 0;
-  const int32_t w = has ? bs.qw[lane] : 0;
+  const int s = has ? sm.qs[lane] : 0;
+  const int32_t w = has ? sm.qw[lane] : 0;
   const bool f = has && member(sm.tile + bs.lo[s], bs.len[s], top, w);
   if (f) {
     atomicAdd(&bs.cnt[s], 1u);
@@ -268,8 +268,8 @@ __device__ __forceinline__ void push(TileSmem& sm, bool pass, int32_t w, int s, 
   if (!m) return;
   if (pass) {
     const int pos = qn + __popc(m & lanemask_lt());
-    bs.qw[pos] = w;
-    bs.qs[pos] = s;
+    sm.qw[pos] = w;
+    sm.qs[pos] = s;
   }
   qn += __popc(m);
   if (qn >= 32) {
@@ -277,13 +277,13 @@ __device__ __forceinline__ void push(TileSmem& sm, bool pass, int32_t w, int s, 
     const int rest = qn - 32;
     int32_t tw = 0, ts = 0;
     if (lane < rest) {
-      tw = bs.qw[32 + lane];
-      ts = bs.qs[32 + lane];
+      tw = sm.qw[32 + lane];
+      ts = sm.qs[32 + lane];
     }
     __syncwarp();
     if (lane < rest) {
-      bs.qw[lane] = tw;
-      bs.qs[lane] = ts;
+      sm.qw[lane] = tw;
+      sm.qs[lane] = ts;
     }
     __syncwarp();
     qn = rest;
@@ -499,7 +499,43 @@ __device__ __forceinline__ uint32_t slot_of(int32_t w) {
   return (static_cast<uint32_t>(w) * 0x9E3779B1u) >> (32 - LOG2);
 }
 
-// Slot of w in the table, or -1.
+// Second choice of a two-choice (cuckoo) table: slot h's partner for key w is
+// h ^ alt_of(w), an odd (so nonzero) offset: the two slots of a key differ and
+// each is the other's partner, so an evicted key finds its other slot from
+// the one it was evicted from.
+template <int LOG2>
+__device__ __forceinline__ uint32_t alt_of(int32_t w) {
+  return ((static_cast<uint32_t>(w) * 0x85EBCA77u) >> (32 - LOG2)) | 1u;
+}
+
+// Cuckoo lookup: slot of w in the table, or -1 -- two independent shared
+// loads, no probe loop, so the lanes of a warp never wait on each other.
+template <int LOG2>
+__device__ __forceinline__ int cuckoo_find(const int32_t* tab, int32_t w) {
+  const uint32_t h1 = slot_of<LOG2>(w), h2 = h1 ^ alt_of<LOG2>(w);
+  const int32_t x1 = tab[h1], x2 = tab[h2];
+  return x1 == w ? static_cast<int>(h1) : (x2 == w ? static_cast<int>(h2) : -1);
+}
+
+// Cuckoo insertion by many threads at once: each thread holds one homeless key
+// and swaps it into its slot; an evicted key moves to its other slot.  Keys are
+// never lost (every move is one atomic exchange).  Returns false if a key is
+// still homeless after kCuckooMoves moves (the caller then rebuilds the chunk
+// with linear probing).
+constexpr int kCuckooMoves = 64;
+template <int LOG2>
+__device__ __forceinline__ bool cuckoo_insert(int32_t* tab, int32_t w) {
+  uint32_t h = slot_of<LOG2>(w);
+  for (int i = 0; i < kCuckooMoves; ++i) {
+    const int32_t old = atomicExch(&tab[h], w);
+    if (old < 0 || old == w) return true;
+    w = old;
+    h ^= alt_of<LOG2>(w);
+  }
+  return false;
+}
+
+// Linear-probing table (fallback when a cuckoo build fails): slot of w, or -1.
 template <int LOG2>
 __device__ __forceinline__ int hash_find(const int32_t* tab, int32_t w) {
   if (w < 0) return -1;
@@ -523,6 +559,13 @@ __device__ __forceinline__ void hash_insert(int32_t* tab, int32_t w) {
   }
 }
 
+// Slot of w in the chunk's table (cuckoo, or linear probing after a failed build).
+template <int LOG2>
+__device__ __forceinline__ int table_find(const int32_t* tab, int32_t w, bool linear) {
+  if (w < 0) return -1;
+  return linear ? hash_find<LOG2>(tab, w) : cuckoo_find<LOG2>(tab, w);
+}
+
 template <int MODE, bool HUB>
 __device__ __forceinline__ void hash_record(BatchSmem& bs, uint32_t* slot_cnt, bool has, int slot, int32_t w, int s,
                                             int32_t v, const CountArgs& a, const CountWs& ws, uint32_t* err) {
@@ -542,7 +585,7 @@ template <int MODE, bool HUB>
 __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab, uint32_t* slot_cnt, int32_t lo,
                                                int32_t hi, int32_t u, bool act, int64_t eg, int32_t v,
                                                const CountArgs& a, const CountWs& ws, uint32_t* err,
-                                               bool chunked, bool first_chunk, int32_t dv) {
+                                               bool chunked, bool first_chunk, int32_t dv, bool linear) {
   constexpr int L = HashCfg<MODE>::kLog2;
   const int lane = lane_id();
   int tot;
@@ -570,7 +613,7 @@ __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab
 #pragma unroll
     for (int k = 0; k < kUnroll; ++k) {
       const int32_t p = p0 + 32 * k + lane;
-      const int slot = (w[k] >= lo && w[k] <= hi) ? hash_find<L>(tab, w[k]) : -1;
+      const int slot = (w[k] >= lo && w[k] <= hi) ? table_find<L>(tab, w[k], linear) : -1;
       hash_record<MODE, HUB>(bs, slot_cnt, p < tot, slot, w[k], s[k], v, a, ws, err);
     }
   }
@@ -590,7 +633,7 @@ __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab
 #pragma unroll
       for (int k = 0; k < kUnroll; ++k) {
         const int32_t p = p0 + 32 * k + lane;
-        const int slot = (w[k] >= lo && w[k] <= hi) ? hash_find<L>(tab, w[k]) : -1;
+        const int slot = (w[k] >= lo && w[k] <= hi) ? table_find<L>(tab, w[k], linear) : -1;
         hash_record<MODE, HUB>(bs, slot_cnt, p < le, slot, w[k], e, v, a, ws, err);
       }
     }
@@ -639,15 +682,23 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
         if (MODE == MODE_LOCAL) slot_cnt[i] = 0;
       }
       __syncthreads();
-      bool bad = false;
+      bool bad = false, homeless = false;
       for (int i = threadIdx.x; i < clen; i += blockDim.x) {
         const int32_t x = a.cols[b + c0 + i];
         if (static_cast<uint32_t>(x) >= static_cast<uint32_t>(a.n)) bad = true;
-        else hash_insert<H::kLog2>(tab, x);
+        else if (!cuckoo_insert<H::kLog2>(tab, x)) homeless = true;
       }
       if (__syncthreads_or(bad)) {
         if (threadIdx.x == 0) set_err(err, ERR_BAD_ID);
         break;
+      }
+      // a cuckoo build that left a key homeless: rebuild this chunk with linear probing
+      const bool linear = __syncthreads_or(homeless);
+      if (linear) {
+        for (int i = threadIdx.x; i < H::kSlots; i += blockDim.x) tab[i] = -1;
+        __syncthreads();
+        for (int i = threadIdx.x; i < clen; i += blockDim.x) hash_insert<H::kLog2>(tab, a.cols[b + c0 + i]);
+        __syncthreads();
       }
       // the chunk is a sorted run of the block vertex's list: its ids lie in [lo, hi]
       const int32_t lo = a.cols[b + c0], hi = a.cols[b + c0 + clen - 1];
@@ -674,7 +725,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
           }
         }
         const uint32_t c = hash_batch<MODE, HUB>(s_b[wid], tab, slot_cnt, lo, hi, x, act, eg, v, a, ws, err,
-                                                 dv > H::kCap, c0 == 0, static_cast<int32_t>(dv));
+                                                 dv > H::kCap, c0 == 0, static_cast<int32_t>(dv), linear);
         cv += c;
         if (act && (MODE == MODE_LOCAL || MODE == MODE_LIST_COUNT) && ws.ecount) {
           // the same lane holds the same edge in every chunk
