@@ -376,6 +376,43 @@ def bench_serving(tc, dev, args):
     return out
 
 
+def run_e2e(args, tc, ctx, dev, edges_host, n, T, q, seed, tri_buf, barrier, world):
+    """The step end to end through the public API: H2D of the edge list and D2H of
+    T_v, C_v and the listing inside the timed region.  Returns ms per step (max over ranks)."""
+    import torch
+    import torch.distributed as dist
+    stream = torch.cuda.current_stream(dev)
+    tv_host = torch.empty(n, dtype=torch.int64).pin_memory()
+    cc_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    tri_host = torch.empty((max(T, 1), 3), dtype=torch.int32).pin_memory()
+
+    def one():
+        ed = edges_host.to(dev, non_blocking=True)
+        g2 = tc.orient(ed, n, ctx)
+        T2, tv2, cc2, tri2 = tc.analyze(g2, True, tri_buf[0], ctx)
+        tc.sparsify_count(g2, q, seed, ctx)
+        tv_host.copy_(tv2, non_blocking=True)
+        cc_host.copy_(cc2, non_blocking=True)
+        tri_host[: len(tri2)].copy_(tri2, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+
+    one()  # untimed: the caching allocator takes this path's device buffers once
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    return e2e_ms
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -488,29 +525,10 @@ def main():
     clocks = sampler.stop()
 
     # ---- e2e: host buffers through the public API, copies inside the timed region ----
-    tv_host = torch.empty(n, dtype=torch.int64).pin_memory()
-    cc_host = torch.empty(n, dtype=torch.float64).pin_memory()
-    tri_host = torch.empty((max(T, 1), 3), dtype=torch.int32).pin_memory()
-    barrier()
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.e2e_steps):
-        ed = edges_host.to(dev, non_blocking=True)
-        g2 = tc.orient(ed, n, ctx)
-        T2, tv2, cc2, tri2 = tc.analyze(g2, True, tri_buf[0], ctx)
-        sp2 = tc.sparsify_count(g2, q, seed, ctx)
-        tv_host.copy_(tv2, non_blocking=True)
-        cc_host.copy_(cc2, non_blocking=True)
-        tri_host[: len(tri2)].copy_(tri2, non_blocking=True)
-        torch.cuda.current_stream(dev).synchronize()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+    e2e_ms = None
+    if args.e2e_steps > 0:
+        e2e_ms = run_e2e(args, tc, ctx, dev, edges_host, n, T, q, seed, tri_buf, barrier, world)
     if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
         mt = torch.tensor([m], device=dev, dtype=torch.int64)
         dist.all_reduce(mt)
         m_total = int(mt.item())
@@ -528,8 +546,9 @@ def main():
 
     # ---- roofline of the intersection kernel (per-vertex counting pass) ----
     peak, peak_src = load_peaks()
-    # every kernel of the per-vertex counting pass: tile, block, hub preparation and hub kernels
-    inter_ms = sum(stages.get(k, (0.0, 0))[0] for k in ("local.tile", "local.block", "local.hub_prep", "local.hub"))
+    # every kernel of the per-vertex counting pass: preparation (int32 offsets, hub
+    # schedule), tile, block and hub kernels
+    inter_ms = sum(stages.get(k, (0.0, 0))[0] for k in ("local.prep", "local.tile", "local.block", "local.hub"))
     inter_calls = max(stages.get("local.tile", (0.0, 0))[1], 1)
     inter_avg_ms = inter_ms / inter_calls
     b_alg = 4 * W + 4 * m + 8 * (n + 1)
@@ -563,8 +582,8 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_count_tile+k_count_block+hub side, per-vertex pass of tc_analyze",
                          "algorithmic_bytes": b_alg, "avg_launch_ms": inter_avg_ms, "peak_source": peak_src},
-            "e2e": {"value": m_total / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "e2e": ({"value": m_total / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms} if e2e_ms else None),
             "gpu_launches": launches,
             "clocks": clocks,
             "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in sorted(stages.items())},

@@ -335,11 +335,21 @@ typedef enum {
   TC_REQ_LIST = 2    /* T and the triangle list (v, u, w) */
 } tc_request_kind;
 
+/*
+ * Slots come in two classes.  Requests on graphs of at most small_edges edges
+ * are small: they run on high-priority streams and may take any free slot.
+ * Large requests take only the low-priority slots; their persistent grids use
+ * 1/grid_div of the GPU each, and their warp-tile blocks retire after a few
+ * vertex chunks, so that the blocks of a small request arriving behind them
+ * are scheduled first as SMs free up.
+ */
 typedef struct {
   int32_t slots;            /* requests on the GPU at once (0 = 8, at most 64) */
   int64_t admit_timeout_ms; /* how long a request may wait for memory before TC_ERR_REJECTED (0 = 10 s) */
-  int32_t grid_div;         /* each request's persistent grids use 1/grid_div of the GPU (0 = 2) */
+  int32_t grid_div;         /* a large request's persistent grids use 1/grid_div of the GPU (0 = 2) */
   int32_t tile_max;         /* as tc_ctx_set_tuning (0 = default) */
+  int32_t high_slots;       /* slots on high-priority streams (0 = half of the slots; < slots) */
+  int64_t small_edges;      /* largest graph (edges) of a small request (0 = 2^21) */
 } tc_serve_config;
 
 typedef struct {

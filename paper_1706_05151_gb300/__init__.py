@@ -58,7 +58,7 @@ class TcResult(ctypes.Structure):
 
 class TcServeConfig(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("admit_timeout_ms", ctypes.c_int64), ("grid_div", ctypes.c_int32),
-                ("tile_max", ctypes.c_int32)]
+                ("tile_max", ctypes.c_int32), ("high_slots", ctypes.c_int32), ("small_edges", ctypes.c_int64)]
 
 
 class TcServeStats(ctypes.Structure):
@@ -496,7 +496,7 @@ class Server:
     """
 
     def __init__(self, pool_bytes: int, slots: int = 8, device: int = 0, admit_timeout_ms: int = 10000,
-                 grid_div: int = 2, tile_max: int = 0):
+                 grid_div: int = 0, tile_max: int = 0, high_slots: int = 0, small_edges: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("libtc needs a CUDA GPU; none is available (there is no CPU fallback)")
         self.lib = load_library()
@@ -504,7 +504,7 @@ class Server:
         self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=self.device)
         torch.cuda.synchronize(self.device)
         h = vp()
-        cfg = TcServeConfig(slots, admit_timeout_ms, grid_div, tile_max)
+        cfg = TcServeConfig(slots, admit_timeout_ms, grid_div, tile_max, high_slots, small_edges)
         st = self.lib.tc_serve_create(device, ctypes.byref(cfg), _ptr(self.pool), self.pool.numel(), ctypes.byref(h))
         if st != 0:
             raise TcError(st, "tc_serve_create failed")

@@ -81,7 +81,8 @@ __device__ __forceinline__ int32_t list_bounds(const CountArgs& a, int32_t u, in
     set_err(err, ERR_BAD_ID);
     return 0;
   }
-  const int64_t lo = a.offsets[u], hi = a.offsets[u + 1];
+  // the int32 copy, when there is one, halves the bytes of this random read
+  const int64_t lo = a.off32 ? a.off32[u] : a.offsets[u], hi = a.off32 ? a.off32[u + 1] : a.offsets[u + 1];
   if (lo < 0 || hi < lo || hi > a.m) {
     set_err(err, ERR_BAD_CSR);
     return 0;
@@ -250,7 +251,7 @@ __device__ __forceinline__ void exact_flush(TileSmem& sm, int cnt, int top, int3
   const int s = has ? sm.qs[lane] : 0;
   const int32_t w = has ? sm.qw[lane] : 0;
   const bool f = has && member(sm.tile + bs.lo[s], bs.len[s], top, w);
-  if (f) {
+  if (f && MODE != MODE_LIST_WRITE) {  // the write pass already knows every count
     atomicAdd(&bs.cnt[s], 1u);
     if (MODE == MODE_LOCAL) atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + w), 1ull);
   }
@@ -374,9 +375,9 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, 
   const int lane = lane_id(), wid = threadIdx.x >> 5;
   TileSmem& sm = s_t[wid];
   unsigned long long acc = 0;
-  for (;;) {
+  for (int32_t chunk = 0; a.tile_quota <= 0 || chunk < a.tile_quota; ++chunk) {
     uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&ws.counters[1], 32u);
+    if (lane == 0) base = atomicAdd(&ws.counters[kCtrCursor], 32u);
     base = __shfl_sync(FULL, base, 0);
     if (base >= static_cast<uint32_t>(a.n)) break;
     const int32_t v = static_cast<int32_t>(base) + lane;
@@ -570,7 +571,7 @@ template <int MODE, bool HUB>
 __device__ __forceinline__ void hash_record(BatchSmem& bs, uint32_t* slot_cnt, bool has, int slot, int32_t w, int s,
                                             int32_t v, const CountArgs& a, const CountWs& ws, uint32_t* err) {
   const bool found = slot >= 0;
-  if (found) {
+  if (found && MODE != MODE_LIST_WRITE) {  // the write pass already knows every count
     atomicAdd(&bs.cnt[s], 1u);
     if (MODE == MODE_LOCAL) atomicAdd(&slot_cnt[slot], 1u);
   }
@@ -655,6 +656,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
   uint32_t* slot_cnt = reinterpret_cast<uint32_t*>(tab + H::kSlots);  // LOCAL only
   __shared__ BatchSmem s_b[kBlockWarps];
   __shared__ unsigned long long s_red[kBlockWarps];
+  __shared__ int64_t s_next;  // next batch of walked lists (warps take batches as they finish)
   const int lane = lane_id(), wid = threadIdx.x >> 5;
   unsigned long long acc = 0;
   const uint32_t qn = HUB ? static_cast<uint32_t>(min64(ws.counters[kCtrItems], ws.items_cap))
@@ -681,6 +683,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
         tab[i] = -1;
         if (MODE == MODE_LOCAL) slot_cnt[i] = 0;
       }
+      if (threadIdx.x == 0) s_next = 0;
       __syncthreads();
       bool bad = false, homeless = false;
       for (int i = threadIdx.x; i < clen; i += blockDim.x) {
@@ -702,7 +705,11 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
       }
       // the chunk is a sorted run of the block vertex's list: its ids lie in [lo, hi]
       const int32_t lo = a.cols[b + c0], hi = a.cols[b + c0 + clen - 1];
-      for (int64_t ub = static_cast<int64_t>(wid) * 32; ub < nl; ub += kBlockWarps * 32) {
+      for (;;) {
+        int64_t ub = 0;
+        if (lane == 0) ub = atomicAdd(reinterpret_cast<unsigned long long*>(&s_next), 32ull);
+        ub = __shfl_sync(FULL, ub, 0);
+        if (ub >= nl) break;
         const int nb = static_cast<int>(min64(32, nl - ub));
         bool act = lane < nb;
         int32_t x = 0;
@@ -764,6 +771,16 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
 // (batch_setup) and flag their apex vertices; the flagged vertices' lists are
 // then walked again to place each such edge in its hub's segment of hub_ent.
 // ---------------------------------------------------------------------------
+
+// int32 copy of the offsets (m < 2^31); an offset outside [0, m] becomes m + 1
+// there, which list_bounds rejects as a broken CSR wherever it is read.
+__global__ void k_off32(int32_t n, int64_t m, const int64_t* __restrict__ offsets, int32_t* __restrict__ off32) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; v <= n; v += stride) {
+    const int64_t o = offsets[v];
+    off32[v] = static_cast<int32_t>((o < 0 || o > m) ? m + 1 : o);
+  }
+}
 
 __global__ void k_hub_list(int32_t n, const int64_t* __restrict__ offsets, int32_t hub_min, CountWs ws) {
   const int lane = lane_id();
@@ -873,22 +890,33 @@ cudaError_t block_smem_optin(Ctx* ctx, size_t smem) {
 template <int MODE>
 cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s) {
   static const char* kNames[4][4] = {
-      {"count.tile", "count.block", "count.hub_prep", "count.hub"},
-      {"local.tile", "local.block", "local.hub_prep", "local.hub"},
-      {"list_count.tile", "list_count.block", "list_count.hub_prep", "list_count.hub"},
-      {"list_write.tile", "list_write.block", "list_write.hub_prep", "list_write.hub"}};
+      {"count.tile", "count.block", "count.prep", "count.hub"},
+      {"local.tile", "local.block", "local.prep", "local.hub"},
+      {"list_count.tile", "list_count.block", "list_count.prep", "list_count.hub"},
+      {"list_write.tile", "list_write.block", "list_write.prep", "list_write.hub"}};
   const bool hub = a.hub_min > 0;
-  const int n_grid = static_cast<int>(min64((static_cast<int64_t>(a.n) + 255) / 256,
+  const int n_grid = static_cast<int>(min64((static_cast<int64_t>(a.n) + 256) / 256,
                                             static_cast<int64_t>(ctx->sm_count) * 8));
-  if (hub) {
+  if (hub || a.off32) {
     Stage st(ctx, s, kNames[MODE][2]);
-    k_hub_list<<<n_grid, 256, 0, s>>>(a.n, a.offsets, a.hub_min, ws);
-    counted(ctx);
+    if (a.off32) {
+      k_off32<<<n_grid, 256, 0, s>>>(a.n, a.m, a.offsets, const_cast<int32_t*>(a.off32));
+      counted(ctx);
+    }
+    if (hub) {
+      k_hub_list<<<n_grid, 256, 0, s>>>(a.n, a.offsets, a.hub_min, ws);
+      counted(ctx);
+    }
   }
   // persistent grids, but no more blocks than there is work for (small graphs leave room for other streams)
-  const int tgrid = static_cast<int>(min64(
-      persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_tile<MODE>), kTileWarps * 32, 0),
-      max64(1, (static_cast<int64_t>(a.n) + 32 * kTileWarps - 1) / (32 * kTileWarps))));
+  // (with a chunk quota, enough blocks that every chunk is taken although each warp stops after its quota)
+  const int64_t chunks = (static_cast<int64_t>(a.n) + 31) / 32;
+  const int tgrid = a.tile_quota > 0
+      ? static_cast<int>(max64(1, (chunks + static_cast<int64_t>(kTileWarps) * a.tile_quota - 1) /
+                                      (static_cast<int64_t>(kTileWarps) * a.tile_quota)))
+      : static_cast<int>(min64(
+            persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_tile<MODE>), kTileWarps * 32, 0),
+            max64(1, (chunks + kTileWarps - 1) / kTileWarps)));
   {
     Stage st(ctx, s, kNames[MODE][0]);
     k_count_tile<MODE><<<tgrid, kTileWarps * 32, 0, s>>>(a, ws, ctx->d_err);
@@ -933,6 +961,7 @@ CountWs carve_count(Carver& c, int32_t n, int64_t m, bool listing) {
   const size_t n1 = static_cast<size_t>(n > 0 ? n : 1), m1 = static_cast<size_t>(m > 0 ? m : 1);
   w.big_queue = c.take<int32_t>(n1);
   w.counters = c.take<uint32_t>(kCtrSlots);
+  w.off32 = c.take<int32_t>(n1 + 1);
   w.hub_idx = c.take<int32_t>(n1);
   w.hubs = c.take<int32_t>(n1);
   w.hub_cnt = c.take<int32_t>(n1);
@@ -967,6 +996,8 @@ cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a_in, CountW
   if (a_in.n <= 0) return cudaGetLastError();
   CountArgs a = a_in;
   a.tile_max = (ctx->tile_max > 0 && ctx->tile_max < kTile) ? ctx->tile_max : kTile;
+  a.tile_quota = ctx->tile_quota;
+  if (ws.off32 && a.m < (int64_t(1) << 31) - 1) a.off32 = ws.off32;  // filled by launch_mode
   // hub side: needs its workspace (absent in the allocation-free entry point)
   a.hub_min = (ws.hub_idx && ctx->hub_min >= 0) ? (ctx->hub_min > 0 ? ctx->hub_min : kHubMinDefault) : 0;
   switch (mode) {

@@ -57,6 +57,7 @@ struct Ctx {
   int32_t tile_max = 0;       // tuning: longest N_v counted by the tile kernel (0 = its capacity)
   int32_t grid_div = 1;       // tuning: persistent grids use 1/grid_div of the resident capacity
   int32_t hub_min = 0;        // tuning: hub side for |N_u| >= hub_min (0: default, -1: off)
+  int32_t tile_quota = 0;     // vertex chunks per warp before a tile-kernel block retires (0: persistent)
   int capturing = 0;          // inside tc_capture_begin .. tc_capture_end
   int saved_async = 0;        // async flag before the capture
   int capture_status = 0;     // first failure inside the capture (0 = none)
@@ -124,6 +125,7 @@ struct CountWs {
   ScanWs scan;          // listing: scan over the m edge counts
   // hub side: edges (v, u) with |N_u| >= hub_min and |N_u| > |N_v| are counted
   // from u's side (NULL hub_idx: off)
+  int32_t* off32;       // offsets as int32 when m < 2^31 (n + 1): half the bytes, L2-resident longer
   int32_t* hub_idx;     // per vertex: its index among the hubs, or -1 (n)
   int32_t* hubs;        // hub vertex of each index (n)
   int32_t* hub_cnt;     // edges counted from each hub's side (n)
@@ -192,6 +194,8 @@ struct CountArgs {
   const int32_t* gid = nullptr;               // ... indexed by the graph id of the apex vertex
   int32_t tile_max = 0;                       // lists longer than this go to the block kernel (set by launch_count)
   int32_t hub_min = 0;                        // hub side for lists of at least this length (0: off; set by launch_count)
+  int32_t tile_quota = 0;                     // chunks per warp before its block retires (0: until the work ends)
+  const int32_t* off32 = nullptr;             // int32 copy of offsets (set by launch_count when m < 2^31)
 };
 cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a, CountWs ws, cudaStream_t s);
 // Listing: eoff = exclusive scan of ecount (after a MODE_LIST_COUNT or MODE_LOCAL pass).

@@ -119,8 +119,11 @@ struct Request {
   Clock::time_point t_submit, t_admit, t_done;
 };
 
+constexpr int32_t kLargeTileQuota = 4;  // vertex chunks per warp before a block of a large request retires
+
 struct Slot {
   cudaStream_t stream = nullptr;
+  bool high = false;            // high-priority stream: small requests only
   tc::Ctx ctx;
   uint64_t* h_total = nullptr;  // pinned
   std::atomic<bool> done{false};
@@ -155,6 +158,7 @@ struct tc_server {
   void* admin_err = nullptr;
   int64_t admitted = 0, completed = 0, rejected = 0, edges_done = 0;
   int64_t admit_timeout_ms = 10000;
+  int64_t small_edges = int64_t(1) << 21;
   size_t resident_bytes = 0;  // resident graphs and slot blocks: memory no request can reclaim
   char last_error[256] = {0};
 };
@@ -332,15 +336,21 @@ void worker_loop(tc_server* s) {
     // 2. admit pending requests while slots and memory allow (in arrival order; a
     //    request that does not fit yet lets later, smaller ones go first)
     for (auto it = s->pending.begin(); it != s->pending.end();) {
-      int free_slot = -1;
-      for (size_t i = 0; i < s->slots.size(); ++i)
-        if (s->slots[i]->ticket < 0) {
-          free_slot = static_cast<int>(i);
-          break;
-        }
-      if (free_slot < 0) break;
       Request& r = s->reqs[*it];
       GraphRec& g = s->graphs[r.graph];
+      // small requests prefer a high-priority slot and may take any; large ones only low-priority slots
+      const bool small = g.m <= s->small_edges;
+      int free_slot = -1;
+      for (size_t i = 0; i < s->slots.size(); ++i) {
+        const Slot& sl = *s->slots[i];
+        if (sl.ticket >= 0 || (sl.high && !small)) continue;
+        if (free_slot < 0 || (sl.high && !s->slots[static_cast<size_t>(free_slot)]->high)) free_slot = static_cast<int>(i);
+      }
+      if (free_slot < 0) {
+        if (small) break;  // every slot is busy
+        ++it;              // no low-priority slot: later small requests may still start
+        continue;
+      }
       const size_t need = footprint(g, r.kind);
       const size_t ws_b = need - (r.kind == TC_REQ_LOCAL ? 16 * static_cast<size_t>(g.n) + 768 : 256);
       void* ws = s->pool.alloc(ws_b);
@@ -389,12 +399,19 @@ tc_status tc_serve_create(int device, const tc_serve_config* cfg, void* pool_dev
   const int slots = cfg && cfg->slots > 0 ? cfg->slots : 8;
   if (slots > 64) return TC_ERR_INVALID_ARG;
   const int64_t admit_timeout = cfg && cfg->admit_timeout_ms > 0 ? cfg->admit_timeout_ms : 10000;
-  const int32_t grid_div = cfg && cfg->grid_div > 0 ? cfg->grid_div : 2;
   const int32_t tile_max = cfg && cfg->tile_max > 0 ? cfg->tile_max : 0;
+  const int32_t high = cfg && cfg->high_slots > 0 ? cfg->high_slots : slots / 2;
+  if (slots > 1 && high >= slots) return TC_ERR_INVALID_ARG;
+  const int32_t n_high = slots > 1 ? high : 0;
+  const int32_t grid_div = cfg && cfg->grid_div > 0 ? cfg->grid_div : 2;
+  if (grid_div > 64) return TC_ERR_INVALID_ARG;
+  int prio_low = 0, prio_high = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
   if (cudaSetDevice(device) != cudaSuccess) return TC_ERR_CUDA;
   tc_server* s = new tc_server();
   s->device = device;
   s->admit_timeout_ms = admit_timeout;
+  if (cfg && cfg->small_edges > 0) s->small_edges = cfg->small_edges;
   s->pool.init(static_cast<char*>(pool_dev), pool_bytes);
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
@@ -413,7 +430,10 @@ tc_status tc_serve_create(int device, const tc_serve_config* cfg, void* pool_dev
   for (int i = 0; i < slots; ++i) {
     Slot* sl = new Slot();
     s->slots.push_back(sl);
-    if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess) return fail_create();
+    sl->high = i < n_high;
+    if (cudaStreamCreateWithPriority(&sl->stream, cudaStreamNonBlocking, sl->high ? prio_high : prio_low) !=
+        cudaSuccess)
+      return fail_create();
     sl->err_block = s->pool.alloc(256);
     if (!sl->err_block) return fail_create();
     if (cudaHostAlloc(reinterpret_cast<void**>(&sl->h_total), 64, cudaHostAllocDefault) != cudaSuccess)
@@ -421,7 +441,10 @@ tc_status tc_serve_create(int device, const tc_serve_config* cfg, void* pool_dev
     sl->ctx.device = device;
     sl->ctx.sm_count = sms;
     sl->ctx.async = 1;
-    sl->ctx.grid_div = grid_div;
+    sl->ctx.grid_div = sl->high ? 1 : grid_div;  // small requests' grids are sized by their work
+    // large requests' tile-kernel blocks retire after a few vertex chunks, so that
+    // blocks of high-priority small requests find free SMs within microseconds
+    sl->ctx.tile_quota = sl->high ? 0 : kLargeTileQuota;
     sl->ctx.tile_max = tile_max;
     sl->ctx.d_err = static_cast<uint32_t*>(sl->err_block);
     sl->ctx.h_err = reinterpret_cast<uint32_t*>(sl->h_total + 4);

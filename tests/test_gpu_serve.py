@@ -44,8 +44,11 @@ def key_of(res):
             None if tri is None else tri.tobytes())
 
 
-def test_results_same_alone_and_in_the_mix(tc):
-    srv = tc.Server(2 << 30, slots=6)
+@pytest.mark.parametrize("small_edges", [0, 1, 40000])
+def test_results_same_alone_and_in_the_mix(tc, small_edges):
+    # small_edges 1: every request is large (low-priority slots, tile blocks with a
+    # chunk quota); 40000: a mix of both classes; 0: the default threshold
+    srv = tc.Server(2 << 30, slots=6, small_edges=small_edges)
     graphs = graph_pool()
     ids = [srv.add_graph(n, e) for n, e in graphs]
     refs = {gid: oracle.count(n, e)["T"] for gid, (n, e) in zip(ids, graphs)}
