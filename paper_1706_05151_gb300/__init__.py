@@ -554,6 +554,9 @@ class Server:
                                           device=self.device).clone()
             elif r.kind == LIST:
                 out.tri = torch.empty((0, 3), dtype=torch.int32, device=self.device)
+            # the clones are queued on PyTorch's stream: they must have read the
+            # server's memory before the ticket (and that memory) is released
+            torch.cuda.current_stream(self.device).synchronize()
         return out
 
     def wait(self, ticket: int, timeout_ms: int = 60000, copy: bool = True, release: bool = True) -> ServeResult:
