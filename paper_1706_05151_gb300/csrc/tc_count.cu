@@ -153,7 +153,8 @@ struct BatchSmem {
 __device__ __forceinline__ void batch_setup(BatchSmem& bs, const CountArgs& a, const CountWs& ws, int32_t u,
                                             bool act, int64_t eg, int32_t salt, int32_t lo, int32_t vlen,
                                             int& tot, bool& is_short, int32_t& len, uint32_t* err, bool list_write,
-                                            uint32_t erun0, int32_t vapex, int32_t dv, int hub_mode) {
+                                            uint32_t erun0, int32_t vapex, int32_t dv, int hub_mode,
+                                            int32_t* excl_out = nullptr) {
   const int lane = lane_id();
   int64_t ub = 0;
   len = 0;
@@ -174,6 +175,7 @@ __device__ __forceinline__ void batch_setup(BatchSmem& bs, const CountArgs& a, c
   const int32_t incl = warp_incl_scan(slen);
   tot = __shfl_sync(FULL, incl, 31);
   const int32_t excl = incl - slen;
+  if (excl_out) *excl_out = excl;
   __syncwarp();
   bs.beg[lane] = is_short ? ub - excl : ub;
   bs.eg[lane] = eg;
@@ -202,11 +204,8 @@ __device__ __forceinline__ unsigned run_mask(int key) {
 
 // Listing: write this lane's triple (if f) at its edge's offset plus the
 // edge's running count; lanes of one edge are contiguous and in candidate order.
-// On the hub side the walked list is N_v of the lane's v and the hashed one N_u
-// of the block's u = `v` here: the triple is (lane's vertex, v, w).
 __device__ __forceinline__ void write_triples(BatchSmem& bs, bool has, bool f, int s, int32_t v, int32_t w,
-                                             const CountArgs& a, const CountWs& ws, uint32_t* err,
-                                             bool hub_side = false) {
+                                             const CountArgs& a, const CountWs& ws, uint32_t* err) {
   const int lane = lane_id();
   const unsigned fm = __ballot_sync(FULL, f);
   if (!fm) return;
@@ -214,8 +213,8 @@ __device__ __forceinline__ void write_triples(BatchSmem& bs, bool has, bool f, i
   if (f) {
     const int64_t idx = bs.ebase[s] + bs.erun[s] + __popc(fm & same & lanemask_lt());
     if (idx < a.cap) {
-      a.tri[3 * idx] = hub_side ? bs.u[s] : v;
-      a.tri[3 * idx + 1] = hub_side ? v : bs.u[s];
+      a.tri[3 * idx] = v;
+      a.tri[3 * idx + 1] = bs.u[s];
       a.tri[3 * idx + 2] = w;
     } else {
       set_err(err, ERR_CAPACITY);
@@ -567,15 +566,71 @@ __device__ __forceinline__ int table_find(const int32_t* tab, int32_t w, bool li
   return linear ? hash_find<LOG2>(tab, w) : cuckoo_find<LOG2>(tab, w);
 }
 
-template <int MODE, bool HUB>
-__device__ __forceinline__ void hash_record(BatchSmem& bs, uint32_t* slot_cnt, bool has, int slot, int32_t w, int s,
-                                            int32_t v, const CountArgs& a, const CountWs& ws, uint32_t* err) {
-  const bool found = slot >= 0;
-  if (found && MODE != MODE_LIST_WRITE) {  // the write pass already knows every count
+// Counting passes of the hash kernels: a match adds to its edge (and, for
+// per-vertex counts, to the slot of w, flushed once per chunk).
+template <int MODE>
+__device__ __forceinline__ void hash_record(BatchSmem& bs, uint32_t* slot_cnt, int slot, int s) {
+  if (slot >= 0) {
     atomicAdd(&bs.cnt[s], 1u);
     if (MODE == MODE_LOCAL) atomicAdd(&slot_cnt[slot], 1u);
   }
-  if (MODE == MODE_LIST_WRITE) write_triples(bs, has, found, s, v, w, a, ws, err, HUB);
+}
+
+// Write pass of the hash kernels, one window of short lists laid end to end
+// (positions wstart .. wstart+31).  The window's lanes map to edges in
+// increasing order, so each edge's lanes form one contiguous run; the edge's
+// output cursor lives in its owner lane's register (wbase: eoff of the edge
+// plus the triples written so far) and a found lane reads its edge's cursor
+// and run start with indexed shuffles -- no shared-memory bookkeeping.
+// Triples of one edge come out in window order, as in every other pass.
+template <bool HUB>
+__device__ __forceinline__ void emit_short(bool f, int s, int32_t w, int32_t wstart, int32_t excl, int32_t slen,
+                                           int32_t u, int32_t v, int64_t& wbase, const CountArgs& a, uint32_t* err) {
+  const int lane = lane_id();
+  const unsigned fm = __ballot_sync(FULL, f);
+  if (!fm) return;
+  // owner lane: its edge's run in this window, clamped to [0, 32)
+  const int32_t first = min(max(excl - wstart, 0), 32), end = min(max(excl + slen - wstart, 0), 32);
+  const unsigned below_end = end >= 32 ? FULL : ((1u << end) - 1u);
+  const unsigned below_first = first >= 32 ? FULL : ((1u << first) - 1u);
+  const int cnt = __popc(fm & below_end & ~below_first);
+  // found lane: cursor and run start of its edge s
+  const int64_t base_s = __shfl_sync(FULL, wbase, s);
+  const int32_t first_s = __shfl_sync(FULL, first, s);
+  const int32_t u_s = __shfl_sync(FULL, u, s);
+  if (f) {
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned run_lo = first_s >= 32 ? FULL : ((1u << first_s) - 1u);
+    const int64_t idx = base_s + __popc(fm & lt & ~run_lo);
+    if (idx < a.cap) {
+      a.tri[3 * idx] = HUB ? u_s : v;
+      a.tri[3 * idx + 1] = HUB ? v : u_s;
+      a.tri[3 * idx + 2] = w;
+    } else {
+      set_err(err, ERR_CAPACITY);
+    }
+  }
+  wbase += cnt;
+}
+
+// Write pass, one window of the long list of edge e (every lane on that edge):
+// base_e is the edge's cursor, kept warp-uniform while the list is walked.
+template <bool HUB>
+__device__ __forceinline__ void emit_long(bool f, int32_t w, int32_t u_e, int32_t v, int64_t& base_e,
+                                          const CountArgs& a, uint32_t* err) {
+  const unsigned fm = __ballot_sync(FULL, f);
+  if (!fm) return;
+  if (f) {
+    const int64_t idx = base_e + __popc(fm & ((1u << lane_id()) - 1u));
+    if (idx < a.cap) {
+      a.tri[3 * idx] = HUB ? u_e : v;
+      a.tri[3 * idx + 1] = HUB ? v : u_e;
+      a.tri[3 * idx + 2] = w;
+    } else {
+      set_err(err, ERR_CAPACITY);
+    }
+  }
+  base_e += __popc(fm);
 }
 
 // One batch of edges against the hashed chunk (ids in [lo, hi]) of the block
@@ -596,8 +651,13 @@ __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab
   const uint32_t erun0 = (MODE == MODE_LIST_WRITE && chunked && !first_chunk && act) ? ws.erun[eg] : 0u;
   // block kernel: edges bound for the hub side are recorded once, with the first chunk
   const int hub_mode = (HUB || a.hub_min <= 0) ? 0 : (first_chunk ? 2 : 1);
+  int32_t excl = 0;
   batch_setup(bs, a, ws, u, act, eg, 0, 0, 0, tot, is_short, len, err, MODE == MODE_LIST_WRITE, erun0, v, dv,
-              hub_mode);
+              hub_mode, &excl);
+  constexpr bool kWrite = MODE == MODE_LIST_WRITE;
+  // write pass: this lane's edge's output cursor (0 for edges without triangles: they have no lanes)
+  int64_t wbase = (kWrite && act && len > 0) ? ws.eoff[eg] + erun0 : 0;
+  const int32_t slen = is_short ? len : 0;
   for (int32_t p0 = 0; p0 < tot; p0 += 32 * kUnroll) {
     int32_t w[kUnroll];
     int s[kUnroll];
@@ -615,7 +675,8 @@ __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab
     for (int k = 0; k < kUnroll; ++k) {
       const int32_t p = p0 + 32 * k + lane;
       const int slot = (w[k] >= lo && w[k] <= hi) ? table_find<L>(tab, w[k], linear) : -1;
-      hash_record<MODE, HUB>(bs, slot_cnt, p < tot, slot, w[k], s[k], v, a, ws, err);
+      if (kWrite) emit_short<HUB>(slot >= 0, s[k], w[k], p0 + 32 * k, excl, slen, u, v, wbase, a, err);
+      else hash_record<MODE>(bs, slot_cnt, slot, s[k]);
     }
   }
   unsigned lm = __ballot_sync(FULL, len > 0 && !is_short);
@@ -624,6 +685,8 @@ __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab
     lm &= lm - 1;
     const int64_t b = bs.beg[e];
     const int32_t le = __shfl_sync(FULL, len, e);
+    const int32_t u_e = __shfl_sync(FULL, u, e);
+    int64_t base_e = __shfl_sync(FULL, wbase, e);
     for (int32_t p0 = 0; p0 < le; p0 += 32 * kUnroll) {
       int32_t w[kUnroll];
 #pragma unroll
@@ -635,12 +698,15 @@ __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab
       for (int k = 0; k < kUnroll; ++k) {
         const int32_t p = p0 + 32 * k + lane;
         const int slot = (w[k] >= lo && w[k] <= hi) ? table_find<L>(tab, w[k], linear) : -1;
-        hash_record<MODE, HUB>(bs, slot_cnt, p < le, slot, w[k], e, v, a, ws, err);
+        if (kWrite) emit_long<HUB>(slot >= 0, w[k], u_e, v, base_e, a, err);
+        else hash_record<MODE>(bs, slot_cnt, slot, e);
       }
     }
+    if (lane == e) wbase = base_e;
   }
   __syncwarp();
-  if (MODE == MODE_LIST_WRITE && chunked && act) ws.erun[eg] = bs.erun[lane];
+  // listing a vertex hashed in several chunks: the next chunk continues at this count
+  if (kWrite && chunked && act && len > 0) ws.erun[eg] = static_cast<uint32_t>(wbase - ws.eoff[eg]);
   return act ? bs.cnt[lane] : 0u;
 }
 
