@@ -132,7 +132,6 @@ __device__ __forceinline__ void fset(uint32_t* bits, int32_t w, int32_t salt) {
 // Per-warp state of one batch of up to 32 oriented edges (v, u), one per lane.
 struct BatchSmem {
   int64_t beg[32];        // short list: start of N_u minus its flattened offset; long list: start of N_u
-  int64_t eg[32];         // global index of the edge (its position in cols)
   int32_t u[32];
   int32_t lo[32];         // tile kernel: N_v's slice [lo, lo + len) of the tile
   int32_t len[32];
@@ -140,7 +139,7 @@ struct BatchSmem {
   uint32_t cnt[32];       // matches of the edge
   uint32_t erun[32];      // listing: triples of the edge written so far
   int64_t ebase[32];      // listing: output offset of the edge
-  uint8_t own[kOwnCap];   // flattened position -> edge, short lists
+  alignas(4) uint8_t own[kOwnCap];  // flattened position -> edge, short lists
 };
 
 // Fills the batch record for this lane's edge; *tot is the flattened length of
@@ -178,7 +177,6 @@ __device__ __forceinline__ void batch_setup(BatchSmem& bs, const CountArgs& a, c
   if (excl_out) *excl_out = excl;
   __syncwarp();
   bs.beg[lane] = is_short ? ub - excl : ub;
-  bs.eg[lane] = eg;
   bs.u[lane] = u;
   bs.lo[lane] = lo;
   bs.len[lane] = vlen;
@@ -186,7 +184,13 @@ __device__ __forceinline__ void batch_setup(BatchSmem& bs, const CountArgs& a, c
   bs.cnt[lane] = 0;
   bs.erun[lane] = erun0;
   if (list_write) bs.ebase[lane] = act ? ws.eoff[eg] : 0;
-  for (int i = 0; i < slen; ++i) bs.own[excl + i] = static_cast<uint8_t>(lane);
+  // owner table: this lane's byte range [excl, excl + slen), whole 32-bit words
+  // where they fit in the range (no other lane writes those words), bytes at the ends
+  int32_t i = 0;
+  for (; i < slen && ((excl + i) & 3); ++i) bs.own[excl + i] = static_cast<uint8_t>(lane);
+  const uint32_t pat = static_cast<uint32_t>(lane) * 0x01010101u;
+  for (; i + 4 <= slen; i += 4) *reinterpret_cast<uint32_t*>(bs.own + excl + i) = pat;
+  for (; i < slen; ++i) bs.own[excl + i] = static_cast<uint8_t>(lane);
   __syncwarp();
 }
 
