@@ -48,6 +48,8 @@ constexpr int kShortLen = 32;        // N_u shorter than this is walked end to e
 constexpr int kOwnCap = 32 * kShortLen;
 constexpr int kTileUnroll = 8;       // candidate windows in flight per lane, tile kernel
 constexpr int kBlockWarps = 8;       // warps per block, block kernel
+constexpr int64_t kBegBias = 1024;   // beg >= -(32 * kShortLen): biased to stay non-negative when packed
+constexpr uint64_t kBegMask = (uint64_t(1) << 58) - 1;
 constexpr int kHubMinDefault = 64;   // default hub_min: lists of at least this many ids take their in-edges
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
@@ -132,6 +134,7 @@ __device__ __forceinline__ void fset(uint32_t* bits, int32_t w, int32_t salt) {
 // Per-warp state of one batch of up to 32 oriented edges (v, u), one per lane.
 struct BatchSmem {
   int64_t beg[32];        // short list: start of N_u minus its flattened offset; long list: start of N_u
+  uint64_t pk[32];        // tile kernel: beg + kBegBias in the low 58 bits, filter salt above (one load for both)
   int32_t u[32];
   int32_t lo[32];         // tile kernel: N_v's slice [lo, lo + len) of the tile
   int32_t len[32];
@@ -181,6 +184,7 @@ __device__ __forceinline__ void batch_setup(BatchSmem& bs, const CountArgs& a, c
   bs.lo[lane] = lo;
   bs.len[lane] = vlen;
   bs.salt[lane] = salt;
+  bs.pk[lane] = static_cast<uint64_t>((is_short ? ub - excl : ub) + kBegBias) | (static_cast<uint64_t>(salt) << 58);
   bs.cnt[lane] = 0;
   bs.erun[lane] = erun0;
   if (list_write) bs.ebase[lane] = act ? ws.eoff[eg] : 0;
@@ -309,22 +313,24 @@ __device__ __forceinline__ uint32_t tile_batch(TileSmem& sm, int top, int32_t u,
   int qn = 0;
   for (int32_t p0 = 0; p0 < tot; p0 += 32 * kTileUnroll) {
     int32_t w[kTileUnroll];
-    int s[kTileUnroll];
+    int ss[kTileUnroll];  // edge (low 8 bits) and its filter salt (above)
 #pragma unroll
     for (int k = 0; k < kTileUnroll; ++k) {
       const int32_t p = p0 + 32 * k + lane;
-      s[k] = 0;
+      ss[k] = 0;
       w[k] = 0;
       if (p < tot) {
-        s[k] = bs.own[p];
-        w[k] = a.cols[bs.beg[s[k]] + p];
+        const int s = bs.own[p];
+        const uint64_t pk = bs.pk[s];
+        w[k] = a.cols[static_cast<int64_t>(pk & kBegMask) - kBegBias + p];
+        ss[k] = s | static_cast<int>(pk >> 58) << 8;
       }
     }
 #pragma unroll
     for (int k = 0; k < kTileUnroll; ++k) {
       const int32_t p = p0 + 32 * k + lane;
-      const bool pass = p < tot && ftest<kTileBitsLog2>(sm.bits, w[k], bs.salt[s[k]]);
-      push<MODE>(sm, pass, w[k], s[k], qn, top, vbase, a, ws, err);
+      const bool pass = p < tot && ftest<kTileBitsLog2>(sm.bits, w[k], ss[k] >> 8);
+      push<MODE>(sm, pass, w[k], ss[k] & 0xff, qn, top, vbase, a, ws, err);
     }
   }
   unsigned lm = __ballot_sync(FULL, len > 0 && !is_short);
