@@ -281,6 +281,35 @@ def bench_batched(tc, ctx, dev, args, rank):
             "batched_edges_per_s": E / (batched_ms * 1e-3), "results_equal": same, "autotune": tuned}
 
 
+def bench_partition(tc, ctx, g, T, dev, parts: int = 8):
+    """The paper's load-balancing step on this graph: parts by the vertex-count
+    scheme (f = 1) and by the work scheme (f = sum over N_v of dhat_v + dhat_u),
+    each part counted by apex range; reports cost and measured-time imbalance
+    (max / mean) and checks that the parts sum to T."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    out = {"parts": parts}
+    for label, cost in (("vertices", tc.COST_VERTICES), ("work", tc.COST_WORK)):
+        b, c = tc.partition(g, parts, cost, ctx)
+        b = b.cpu().numpy()
+        c = c.cpu().numpy().astype(np.float64)
+        total = torch.zeros(1, dtype=torch.int64, device=dev)
+        ms = []
+        for j in range(parts):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tc.count_range(g, int(b[j]), int(b[j + 1]), total, None, ctx)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        ms = np.array(ms)
+        out[label] = {"bounds": [int(x) for x in b], "cost_imbalance": float(c.max() / max(c.mean(), 1e-30)),
+                      "part_ms": [round(float(x), 3) for x in ms],
+                      "time_imbalance": float(ms.max() / max(ms.mean(), 1e-30)),
+                      "parts_sum_to_T": int(total.item()) == T}
+    return out
+
+
 def serving_pool():
     """The serving configuration's graph pool (seeded): ER n = 2^12..2^18 with mean
     degree 16, R-MAT scale 16..20 with edge factor 16, Chung-Lu (gamma 2.1) with
@@ -434,6 +463,8 @@ def main():
     ap.add_argument("--serve-loads", default="0.5,0.85", help="arrival rates as fractions of measured capacity")
     ap.add_argument("--serve-pool-gb", type=float, default=150.0)
     ap.add_argument("--no-tune", action="store_true", help="skip the tile/block threshold autotuner")
+    ap.add_argument("--no-partition", dest="partition", action="store_false",
+                    help="skip the load-balancing partition report")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -535,6 +566,8 @@ def main():
     else:
         m_total = m
 
+    part = bench_partition(tc, ctx, g, T, dev) if world == 1 and args.partition else None
+
     batched = None
     if args.batch_graphs > 0:
         batched = bench_batched(tc, ctx, dev, args, rank)
@@ -588,6 +621,7 @@ def main():
             "clocks": clocks,
             "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in sorted(stages.items())},
             "cpu_baseline": cpu,
+            "partition": part,
             "batched": batched,
             "serving": serving,
             "sparsified": {"kept_edges": sp[1], "kept_triangles": sp[0], "estimate": sp[2],

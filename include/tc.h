@@ -59,7 +59,8 @@ typedef enum {
   TC_OP_COUNT = 1,       /* tc_count and tc_count_local */
   TC_OP_LIST = 2,        /* tc_list, tc_list_count, tc_list_write, tc_analyze */
   TC_OP_SPARSIFY = 3,    /* tc_sparsify_count */
-  TC_OP_BATCH = 4        /* tc_batch: n = total vertices N, m = total edges E */
+  TC_OP_BATCH = 4,       /* tc_batch: n = total vertices N, m = total edges E */
+  TC_OP_PARTITION = 5    /* tc_partition */
 } tc_op;
 
 typedef struct tc_ctx tc_ctx;
@@ -244,6 +245,50 @@ tc_status tc_analyze(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, int64_
 tc_status tc_sparsify_count(tc_ctx* ctx, const tc_graph* g, double q, uint64_t seed,
                             uint64_t* kept_tri_dev, int64_t* kept_edges_dev, void* ws, size_t ws_bytes,
                             tc_stream stream);
+
+/* ---- cost-balanced partition of the apex vertices (Section "load balancing") --- */
+
+/*
+ * Cost functions f(v) of Table "lbscheme" (the paper's load-balancing schemes).
+ * WORK is the scheme whose f(v) = sum over u in N_v of (dhat_v + dhat_u): the
+ * reads of Theorem 2 charged to apex v, the per-vertex counting work.
+ */
+typedef enum {
+  TC_COST_VERTICES = 0,  /* f(v) = 1 */
+  TC_COST_DEGREE = 1,    /* f(v) = d_v (needs g->deg) */
+  TC_COST_DHAT = 2,      /* f(v) = dhat_v */
+  TC_COST_DEG_DHAT = 3,  /* f(v) = d_v * dhat_v (needs g->deg) */
+  TC_COST_DHAT_SQ = 4,   /* f(v) = dhat_v^2 */
+  TC_COST_WORK = 5       /* f(v) = sum_{u in N_v} (dhat_v + dhat_u) */
+} tc_cost;
+
+/*
+ * Split the vertices into `parts` contiguous ranges of about equal cost, as the
+ * paper's partitioning step does: F(t) = f(0) + ... + f(t), alpha = F(n-1) /
+ * parts, and the boundary node of part j (0 < j < parts) is the smallest v
+ * with F(v) >= j * alpha (compared exactly in integers); part j is
+ * [bounds[j], bounds[j+1]), bounds[0] = 0, bounds[parts] = n.  dhat is taken
+ * from the offsets.
+ *   parts          1 .. 65536
+ *   bounds_dev     device int64[parts + 1]
+ *   part_cost_dev  device uint64[parts] (sum of f over each part) or NULL
+ * Workspace: tc_workspace_size(TC_OP_PARTITION, n, m).
+ */
+tc_status tc_partition(tc_ctx* ctx, const tc_graph* g, int32_t parts, int cost, int64_t* bounds_dev,
+                       uint64_t* part_cost_dev, void* ws, size_t ws_bytes, tc_stream stream);
+
+/*
+ * The triangles whose first vertex in the order of Eq. (1) -- the apex v of
+ * the counting loop of Figure 2 -- lies in [v_begin, v_end): one part of a
+ * partition, as one processor of the paper counts its core vertices.  Summed
+ * over the parts of any partition of [0, n) they give T and T_v exactly.
+ * ADDS to its outputs (the caller clears them once, then runs the parts):
+ *   total_dev device uint64[1] += the part's triangles;
+ *   tv_dev    device int64[n] or NULL: += each vertex's triangles of the part.
+ * Workspace: tc_workspace_size(TC_OP_COUNT, n, m).
+ */
+tc_status tc_count_range(tc_ctx* ctx, const tc_graph* g, int32_t v_begin, int32_t v_end, uint64_t* total_dev,
+                         int64_t* tv_dev, void* ws, size_t ws_bytes, tc_stream stream);
 
 /* ---- batched form ------------------------------------------------------------ */
 

@@ -207,3 +207,68 @@ def sparsify_count(n: int, edges, seed: int, q: float):
     _check(_load().orc_sparsify_count(int(n), len(e), _p(e, i32p), int(seed), float(q),
                                       ctypes.byref(T), ctypes.byref(mk), ctypes.byref(est)))
     return int(T.value), int(mk.value), float(est.value)
+
+
+# ---- load-balancing partition (Section "load balancing", Table "lbscheme") ----
+
+COST_VERTICES, COST_DEGREE, COST_DHAT, COST_DEG_DHAT, COST_DHAT_SQ, COST_WORK = 0, 1, 2, 3, 4, 5
+
+
+def partition_costs(n: int, edges, cost: int) -> np.ndarray:
+    """f(v) of the paper's load-balancing schemes (Table "lbscheme"), with d_v the
+    degree and dhat_v = |N_v| of the degree-ordered orientation:
+    1, d_v, dhat_v, d_v * dhat_v, dhat_v^2, and sum over u in N_v of (dhat_v + dhat_u)."""
+    adj = Adjacency(n, edges)
+    off, cols, dhat = adj.orient()
+    deg = adj.deg.astype(np.int64)
+    dh = dhat.astype(np.int64)
+    if cost == COST_VERTICES:
+        return np.ones(n, dtype=np.int64)
+    if cost == COST_DEGREE:
+        return deg
+    if cost == COST_DHAT:
+        return dh
+    if cost == COST_DEG_DHAT:
+        return deg * dh
+    if cost == COST_DHAT_SQ:
+        return dh * dh
+    if cost == COST_WORK:
+        f = np.zeros(n, dtype=np.int64)
+        for v in range(n):
+            for u in cols[off[v]:off[v + 1]]:
+                f[v] += dh[v] + dh[u]
+        return f
+    raise ValueError("unknown cost function")
+
+
+def partition(n: int, edges, parts: int, cost: int):
+    """The paper's partition of V into `parts` contiguous ranges: F(t) = f(0) + ... + f(t),
+    alpha = F(n-1) / parts, and the boundary node of part j (0 < j < parts) is the
+    smallest v with F(v) >= j * alpha (n if there is none); bounds[0] = 0,
+    bounds[parts] = n.  Returns (bounds int64[parts+1], part costs int64[parts])."""
+    f = partition_costs(n, edges, cost)
+    F = np.cumsum(f) if n else np.zeros(0, dtype=np.int64)
+    total = int(F[-1]) if n else 0
+    bounds = [0]
+    for j in range(1, parts):
+        x = n
+        for v in range(n):          # smallest v with parts * F(v) >= j * total, in exact integers
+            if parts * int(F[v]) >= j * total:
+                x = v
+                break
+        bounds.append(x)
+    bounds.append(n)
+    Fx = np.concatenate([[0], F]).astype(np.int64)
+    costs = np.array([Fx[bounds[j + 1]] - Fx[bounds[j]] for j in range(parts)], dtype=np.int64)
+    return np.array(bounds, dtype=np.int64), costs
+
+
+def count_apex_range(n: int, edges, lo: int, hi: int):
+    """Triangles whose first vertex in the order of Eq. (1) lies in [lo, hi), and each
+    vertex's share of them: (count, tv int64[n]), from NodeIterator++'s listing, whose
+    triples are written in that order (first vertex first)."""
+    r = count(n, edges, listing=True)
+    tri = r["tri"]
+    sel = tri[(tri[:, 0] >= lo) & (tri[:, 0] < hi)]
+    tv = np.bincount(sel.ravel(), minlength=n).astype(np.int64) if len(sel) else np.zeros(n, np.int64)
+    return int(len(sel)), tv

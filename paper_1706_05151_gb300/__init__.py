@@ -25,7 +25,9 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtc.so")
 
-TC_OP_ORIENT, TC_OP_COUNT, TC_OP_LIST, TC_OP_SPARSIFY, TC_OP_BATCH = 0, 1, 2, 3, 4
+TC_OP_ORIENT, TC_OP_COUNT, TC_OP_LIST, TC_OP_SPARSIFY, TC_OP_BATCH, TC_OP_PARTITION = 0, 1, 2, 3, 4, 5
+# cost functions of the paper's load-balancing schemes (Table "lbscheme"), as tc_cost
+COST_VERTICES, COST_DEGREE, COST_DHAT, COST_DEG_DHAT, COST_DHAT_SQ, COST_WORK = 0, 1, 2, 3, 4, 5
 STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_INVALID_GRAPH", 3: "TC_ERR_WORKSPACE",
           4: "TC_ERR_CAPACITY", 5: "TC_ERR_CUDA", 6: "TC_ERR_UNSUPPORTED", 7: "TC_ERR_TIMEOUT",
           8: "TC_ERR_REJECTED", 9: "TC_ERR_NOT_READY"}
@@ -39,7 +41,7 @@ EXPORTS = ["tc_ctx_create", "tc_ctx_destroy", "tc_ctx_set_async", "tc_ctx_status
            "tc_serve_stats",
            "tc_ctx_set_tuning", "tc_ctx_set_hub_min", "tc_ctx_set_profiling", "tc_ctx_stage_count", "tc_ctx_stage", "tc_ctx_reset_stats", "tc_ctx_launches",
            "tc_count_static", "tc_capture_begin", "tc_capture_end", "tc_exec_launch", "tc_exec_kernels",
-           "tc_exec_destroy"]
+           "tc_exec_destroy", "tc_partition", "tc_count_range"]
 
 
 class TcError(RuntimeError):
@@ -107,6 +109,8 @@ def load_library(path: str = LIB_PATH):
             "tc_list": (i32, [vp, G, vp, i64, ctypes.POINTER(i64), vp, sz, vp]),
             "tc_analyze": (i32, [vp, G, vp, vp, vp, vp, i64, ctypes.POINTER(i64), vp, sz, vp]),
             "tc_batch": (i32, [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+            "tc_partition": (i32, [vp, G, i32, ctypes.c_int, vp, vp, vp, sz, vp]),
+            "tc_count_range": (i32, [vp, G, i32, i32, vp, vp, vp, sz, vp]),
             "tc_capture_begin": (i32, [vp, vp]),
             "tc_capture_end": (i32, [vp, vp, ctypes.POINTER(vp)]),
             "tc_exec_launch": (i32, [vp, vp]),
@@ -359,6 +363,27 @@ def sparsify_count(g: Graph, q: float, seed: int, ctx: Context | None = None):
     t = int(kept_tri.item())
     est = float(t) / (q * q * q) if q > 0 else float("nan")
     return t, int(kept_edges.item()), est
+
+
+def partition(g: Graph, parts: int, cost: int = COST_WORK, ctx: Context | None = None):
+    """tc_partition: (bounds int64[parts+1], per-part cost uint64[parts] as int64) on the device."""
+    ctx = ctx or default_context()
+    bounds = torch.empty(parts + 1, dtype=torch.int64, device=ctx.device)
+    costs = torch.empty(parts, dtype=torch.int64, device=ctx.device)
+    ws = ctx.workspace(TC_OP_PARTITION, g.n, g.m)
+    ctx.check(ctx.lib.tc_partition(ctx.handle, ctypes.byref(g.struct()), parts, cost, _ptr(bounds), _ptr(costs),
+                                   _ptr(ws), ws.numel(), _stream(ctx.device)))
+    return bounds, costs
+
+
+def count_range(g: Graph, v_begin: int, v_end: int, total: torch.Tensor, tv: torch.Tensor | None = None,
+                ctx: Context | None = None):
+    """tc_count_range: ADD the triangles whose apex is in [v_begin, v_end) to total (int64[1])
+    and, if given, each vertex's share to tv (int64[n])."""
+    ctx = ctx or default_context()
+    ws = ctx.workspace(TC_OP_COUNT, g.n, g.m)
+    ctx.check(ctx.lib.tc_count_range(ctx.handle, ctypes.byref(g.struct()), int(v_begin), int(v_end), _ptr(total),
+                                     _ptr(tv), _ptr(ws), ws.numel(), _stream(ctx.device)))
 
 
 @dataclass

@@ -270,6 +270,7 @@ tc_status tc_workspace_size(tc_op op, int32_t n, int64_t m, size_t* bytes) {
     case TC_OP_LIST: tc::carve_count(c, n, m, true); break;
     case TC_OP_SPARSIFY: tc::carve_sparsify(c, n, m); break;
     case TC_OP_BATCH: tc::carve_batch(c, n, m); break;
+    case TC_OP_PARTITION: tc::carve_partition(c, n); break;
     default: return TC_ERR_INVALID_ARG;
   }
   *bytes = c.size();
@@ -313,6 +314,44 @@ static tc_status count_impl(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev,
   e = tc::launch_count(ctx, local ? tc::MODE_LOCAL : tc::MODE_COUNT, a, w, s);
   if (e == cudaSuccess && cc_dev) e = tc::launch_clustering(ctx, g->n, g->deg, tv_dev, cc_dev, s);
   return finish(ctx, s, e);
+}
+
+tc_status tc_count_range(tc_ctx* ctx, const tc_graph* g, int32_t v_begin, int32_t v_end, uint64_t* total_dev,
+                         int64_t* tv_dev, void* ws, size_t ws_bytes, tc_stream stream) {
+  tc_status st = check_graph(ctx, g);
+  if (st != TC_OK) return st;
+  if (!total_dev) return fail(ctx, TC_ERR_INVALID_ARG, "total_dev is NULL");
+  if (v_begin < 0 || v_end < v_begin || v_end > g->n)
+    return fail(ctx, TC_ERR_INVALID_ARG, "need 0 <= v_begin <= v_end <= n");
+  if ((st = check_ws(ctx, TC_OP_COUNT, g->n, g->m, ws, ws_bytes)) != TC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = begin(ctx, s)) != TC_OK) return st;
+  if (v_begin == v_end) return finish(ctx, s, cudaSuccess);
+  Carver c(ws);
+  tc::CountWs w = tc::carve_count(c, g->n, g->m, false);
+  tc::CountArgs a{g->n, g->m, g->offsets, g->cols, reinterpret_cast<unsigned long long*>(total_dev), tv_dev,
+                  nullptr, 0};
+  a.v_lo = v_begin;
+  a.v_hi = v_end;
+  return finish(ctx, s, tc::launch_count(ctx, tv_dev ? tc::MODE_LOCAL : tc::MODE_COUNT, a, w, s));
+}
+
+tc_status tc_partition(tc_ctx* ctx, const tc_graph* g, int32_t parts, int cost, int64_t* bounds_dev,
+                       uint64_t* part_cost_dev, void* ws, size_t ws_bytes, tc_stream stream) {
+  tc_status st = check_graph(ctx, g);
+  if (st != TC_OK) return st;
+  if (parts < 1 || parts > 65536) return fail(ctx, TC_ERR_INVALID_ARG, "parts must be in [1, 65536]");
+  if (cost < TC_COST_VERTICES || cost > TC_COST_WORK) return fail(ctx, TC_ERR_INVALID_ARG, "unknown cost function");
+  if ((cost == TC_COST_DEGREE || cost == TC_COST_DEG_DHAT) && g->n > 0 && !g->deg)
+    return fail(ctx, TC_ERR_INVALID_ARG, "this cost function needs g->deg");
+  if (!bounds_dev) return fail(ctx, TC_ERR_INVALID_ARG, "bounds_dev is NULL");
+  if ((st = check_ws(ctx, TC_OP_PARTITION, g->n, g->m, ws, ws_bytes)) != TC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = begin(ctx, s)) != TC_OK) return st;
+  Carver c(ws);
+  tc::PartitionWs w = tc::carve_partition(c, g->n);
+  return finish(ctx, s, tc::launch_partition(ctx, g->n, g->m, g->offsets, g->cols, g->deg, cost, parts, bounds_dev,
+                                             part_cost_dev, w, s));
 }
 
 tc_status tc_count(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, void* ws, size_t ws_bytes, tc_stream stream) {

@@ -385,12 +385,13 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, 
   TileSmem& sm = s_t[wid];
   unsigned long long acc = 0;
   for (int32_t chunk = 0; a.tile_quota <= 0 || chunk < a.tile_quota; ++chunk) {
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&ws.counters[kCtrCursor], 32u);
-    base = __shfl_sync(FULL, base, 0);
-    if (base >= static_cast<uint32_t>(a.n)) break;
+    uint32_t off = 0;
+    if (lane == 0) off = atomicAdd(&ws.counters[kCtrCursor], 32u);
+    off = __shfl_sync(FULL, off, 0);
+    if (off >= static_cast<uint32_t>(a.v_hi - a.v_lo)) break;
+    const uint32_t base = static_cast<uint32_t>(a.v_lo) + off;  // apex vertices [v_lo, v_hi) only
     const int32_t v = static_cast<int32_t>(base) + lane;
-    const bool valid = v < a.n;
+    const bool valid = v < a.v_hi;
     int64_t b = 0, e = 0;
     if (valid) {
       b = a.offsets[v];
@@ -986,7 +987,7 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
   }
   // persistent grids, but no more blocks than there is work for (small graphs leave room for other streams)
   // (with a chunk quota, enough blocks that every chunk is taken although each warp stops after its quota)
-  const int64_t chunks = (static_cast<int64_t>(a.n) + 31) / 32;
+  const int64_t chunks = (static_cast<int64_t>(a.v_hi) - a.v_lo + 31) / 32;
   const int tgrid = a.tile_quota > 0
       ? static_cast<int>(max64(1, (chunks + static_cast<int64_t>(kTileWarps) * a.tile_quota - 1) /
                                       (static_cast<int64_t>(kTileWarps) * a.tile_quota)))
@@ -1071,6 +1072,8 @@ cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a_in, CountW
   if (e != cudaSuccess) return e;
   if (a_in.n <= 0) return cudaGetLastError();
   CountArgs a = a_in;
+  if (a.v_hi < 0) a.v_hi = a.n;
+  if (a.v_lo < 0 || a.v_lo > a.v_hi || a.v_hi > a.n) return cudaErrorInvalidValue;
   a.tile_max = (ctx->tile_max > 0 && ctx->tile_max < kTile) ? ctx->tile_max : kTile;
   a.tile_quota = ctx->tile_quota;
   if (ws.off32 && a.m < (int64_t(1) << 31) - 1) a.off32 = ws.off32;  // filled by launch_mode

@@ -159,6 +159,16 @@ struct SparsifyWs {
 };
 SparsifyWs carve_sparsify(Carver& c, int32_t n, int64_t m);
 
+struct PartitionWs {
+  int64_t* f;           // cost of each vertex (n)
+  int64_t* F;           // exclusive scan of f (n + 1)
+  ScanWs scan;
+};
+PartitionWs carve_partition(Carver& c, int32_t n);
+cudaError_t launch_partition(Ctx* ctx, int32_t n, int64_t m, const int64_t* offsets, const int32_t* cols,
+                             const int32_t* deg, int cost, int32_t parts, int64_t* bounds, uint64_t* part_cost,
+                             PartitionWs ws, cudaStream_t s);
+
 struct BatchWs {
   int32_t* edges;       // union edge list with global ids (2E)
   int32_t* gid;         // graph id per global vertex (N)
@@ -196,6 +206,7 @@ struct CountArgs {
   int32_t hub_min = 0;                        // hub side for lists of at least this length (0: off; set by launch_count)
   int32_t tile_quota = 0;                     // chunks per warp before its block retires (0: until the work ends)
   const int32_t* off32 = nullptr;             // int32 copy of offsets (set by launch_count when m < 2^31)
+  int32_t v_lo = 0, v_hi = -1;                // apex vertices counted: [v_lo, v_hi) (-1: n)
 };
 cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a, CountWs ws, cudaStream_t s);
 // Listing: eoff = exclusive scan of ecount (after a MODE_LIST_COUNT or MODE_LOCAL pass).

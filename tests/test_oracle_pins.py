@@ -335,3 +335,54 @@ def test_clique_with_pendants_closed_form():
             tris = triangles_by_triples(n, e)
             assert len(tris) == T
             assert np.array_equal(per_vertex_from_list(n, tris), tv)
+
+
+# ---- load-balancing partition (Table "lbscheme", the boundary-node definition) ----
+
+def _fraction_bounds(F, parts):
+    """Boundary nodes straight from the definition, with rational arithmetic:
+    x_j = min{v : F(v) >= j * alpha}, alpha = F(n-1) / parts."""
+    from fractions import Fraction
+    n = len(F)
+    alpha = Fraction(int(F[-1]), parts) if n else Fraction(0)
+    out = [0]
+    for j in range(1, parts):
+        out.append(next((v for v in range(n) if F[v] >= j * alpha), n))
+    return out + [n]
+
+
+@pytest.mark.parametrize("cost", range(6))
+def test_partition_follows_the_boundary_definition(cost):
+    for n, e in ((50, synth.er(50, 300, 1)), (120, synth.ba(120, 3, 2)), (256, synth.rmat(8, 6, 3)),
+                 (7, synth.star(6)), (12, np.zeros((0, 2), np.int32))):
+        f = oracle.partition_costs(n, e, cost)
+        F = np.cumsum(f)
+        for parts in (1, 2, 5, 16, n + 3):
+            b, c = oracle.partition(n, e, parts, cost)
+            assert list(b) == _fraction_bounds(F, parts)
+            assert b[0] == 0 and b[-1] == n and all(b[i] <= b[i + 1] for i in range(parts))
+            assert int(c.sum()) == (int(F[-1]) if n else 0)
+
+
+def test_partition_costs_match_their_closed_sums():
+    n, e = 256, synth.rmat(8, 10, 4)
+    adj = oracle.Adjacency(n, e)
+    m = len(e)
+    assert oracle.partition_costs(n, e, oracle.COST_VERTICES).sum() == n
+    assert oracle.partition_costs(n, e, oracle.COST_DEGREE).sum() == 2 * m
+    assert oracle.partition_costs(n, e, oracle.COST_DHAT).sum() == m           # sum dhat = m
+    # sum over v, u in N_v of (dhat_v + dhat_u) = sum_v d_v dhat_v (Theorem 2's cost)
+    assert oracle.partition_costs(n, e, oracle.COST_WORK).sum() == adj.cost()
+    assert oracle.partition_costs(n, e, oracle.COST_DEG_DHAT).sum() == adj.cost()
+
+
+def test_apex_ranges_sum_to_the_whole():
+    n, e = 128, synth.rmat(7, 12, 5)
+    ref = oracle.count(n, e, local=True)
+    total, tv = 0, np.zeros(n, np.int64)
+    for lo, hi in ((0, 17), (17, 17), (17, 90), (90, 128)):
+        c, t = oracle.count_apex_range(n, e, lo, hi)
+        total += c
+        tv += t
+    assert total == ref["T"]
+    assert np.array_equal(tv, ref["tv"])
