@@ -310,6 +310,35 @@ def bench_partition(tc, ctx, g, T, dev, parts: int = 8):
     return out
 
 
+def bench_orders(tc, ctx, edges_dev, n, T, dev, seed):
+    """Section "An Optimal Node Ordering" on this graph: the counting cost
+    W = sum_v d_v * dhat_v and the measured orientation and count times under
+    the id, degree and random orders (Theorem 3: the degree order minimises W)."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    g0 = tc.orient(edges_dev, n, ctx)
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    keys = {"id": torch.zeros(n, dtype=torch.int64, device=dev),
+            "degree": g0.deg.to(torch.int64),
+            "random": torch.randperm(n, generator=gen).to(dev)}
+    del g0
+    out = {}
+    for name, k in keys.items():
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        g = tc.orient(edges_dev, n, ctx, keys=k)
+        e1.record(stream)
+        t = tc.count(g, ctx)
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        W = int((g.deg.to(torch.int64) * g.dhat.to(torch.int64)).sum().item())
+        out[name] = {"W": W, "orient_ms": round(e0.elapsed_time(e1), 3), "count_ms": round(e1.elapsed_time(e2), 3),
+                     "triangles_equal": t == T}
+        del g
+        torch.cuda.empty_cache()
+    return out
+
+
 def serving_pool():
     """The serving configuration's graph pool (seeded): ER n = 2^12..2^18 with mean
     degree 16, R-MAT scale 16..20 with edge factor 16, Chung-Lu (gamma 2.1) with
@@ -465,6 +494,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the tile/block threshold autotuner")
     ap.add_argument("--no-partition", dest="partition", action="store_false",
                     help="skip the load-balancing partition report")
+    ap.add_argument("--no-orders", dest="orders", action="store_false",
+                    help="skip the node-ordering report (id, degree, random orders)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -567,6 +598,7 @@ def main():
         m_total = m
 
     part = bench_partition(tc, ctx, g, T, dev) if world == 1 and args.partition else None
+    orders = bench_orders(tc, ctx, edges_dev, n, T, dev, args.seed) if world == 1 and args.orders else None
 
     batched = None
     if args.batch_graphs > 0:
@@ -622,6 +654,7 @@ def main():
             "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in sorted(stages.items())},
             "cpu_baseline": cpu,
             "partition": part,
+            "orders": orders,
             "batched": batched,
             "serving": serving,
             "sparsified": {"kept_edges": sp[1], "kept_triangles": sp[0], "estimate": sp[2],

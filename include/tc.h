@@ -169,6 +169,20 @@ tc_status tc_orient(tc_ctx* ctx, int32_t n, int64_t m, const int32_t* edges, int
                     int32_t* cols, int32_t* deg, int32_t* dhat, void* ws, size_t ws_bytes,
                     tc_stream stream);
 
+/*
+ * Orientation by another total order (Section "An Optimal Node Ordering": any
+ * order counts each triangle once; Theorem 3: the degree order minimises the
+ * counting cost sum_v d_v * dhat_v).  u precedes v iff keys[u] < keys[v], or
+ * keys[u] = keys[v] and u < v.  keys_dev: device int64[n]; NULL gives the
+ * degree order (= tc_orient).  Examples: all keys equal -- the id order; a
+ * random permutation -- a random order; d_v -- Eq. (1).  Everything else as
+ * tc_orient (deg is still the degree).  The counting calls work on any such
+ * orientation.
+ */
+tc_status tc_orient_by(tc_ctx* ctx, int32_t n, int64_t m, const int32_t* edges, const int64_t* keys_dev,
+                       int64_t* offsets, int32_t* cols, int32_t* deg, int32_t* dhat, void* ws, size_t ws_bytes,
+                       tc_stream stream);
+
 /* ---- counting (Figure 2 counting loop; Theorems 1-2) --------------------- */
 
 /*

@@ -41,7 +41,7 @@ EXPORTS = ["tc_ctx_create", "tc_ctx_destroy", "tc_ctx_set_async", "tc_ctx_status
            "tc_serve_stats",
            "tc_ctx_set_tuning", "tc_ctx_set_hub_min", "tc_ctx_set_profiling", "tc_ctx_stage_count", "tc_ctx_stage", "tc_ctx_reset_stats", "tc_ctx_launches",
            "tc_count_static", "tc_capture_begin", "tc_capture_end", "tc_exec_launch", "tc_exec_kernels",
-           "tc_exec_destroy", "tc_partition", "tc_count_range"]
+           "tc_exec_destroy", "tc_partition", "tc_count_range", "tc_orient_by"]
 
 
 class TcError(RuntimeError):
@@ -109,6 +109,7 @@ def load_library(path: str = LIB_PATH):
             "tc_list": (i32, [vp, G, vp, i64, ctypes.POINTER(i64), vp, sz, vp]),
             "tc_analyze": (i32, [vp, G, vp, vp, vp, vp, i64, ctypes.POINTER(i64), vp, sz, vp]),
             "tc_batch": (i32, [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+            "tc_orient_by": (i32, [vp, i32, i64, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
             "tc_partition": (i32, [vp, G, i32, ctypes.c_int, vp, vp, vp, sz, vp]),
             "tc_count_range": (i32, [vp, G, i32, i32, vp, vp, vp, sz, vp]),
             "tc_capture_begin": (i32, [vp, vp]),
@@ -258,8 +259,9 @@ class Graph:
                        self.dhat.data_ptr() if self.dhat is not None else None)
 
 
-def orient(edges: torch.Tensor, n: int, ctx: Context | None = None) -> Graph:
-    """tc_orient: edges int32[m, 2] on the GPU (each undirected edge once) -> oriented CSR."""
+def orient(edges: torch.Tensor, n: int, ctx: Context | None = None, keys: torch.Tensor | None = None) -> Graph:
+    """tc_orient: edges int32[m, 2] on the GPU (each undirected edge once) -> oriented CSR.
+    With keys (int64[n] on the GPU), tc_orient_by: v before u iff (keys[v], v) < (keys[u], u)."""
     ctx = ctx or default_context()
     dev = ctx.device
     if edges.device != dev or edges.dtype != torch.int32 or edges.dim() != 2 or edges.shape[1] != 2:
@@ -271,8 +273,15 @@ def orient(edges: torch.Tensor, n: int, ctx: Context | None = None) -> Graph:
     deg = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
     dhat = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
     ws = ctx.workspace(TC_OP_ORIENT, n, m)
-    ctx.check(ctx.lib.tc_orient(ctx.handle, n, m, _ptr(edges) if m else None, _ptr(offsets), _ptr(cols),
-                                _ptr(deg), _ptr(dhat), _ptr(ws), ws.numel(), _stream(dev)))
+    if keys is None:
+        ctx.check(ctx.lib.tc_orient(ctx.handle, n, m, _ptr(edges) if m else None, _ptr(offsets), _ptr(cols),
+                                    _ptr(deg), _ptr(dhat), _ptr(ws), ws.numel(), _stream(dev)))
+    else:
+        if keys.device != dev or keys.dtype != torch.int64 or keys.shape != (n,):
+            raise ValueError("keys must be an int64 [n] tensor on the context's device")
+        keys = keys.contiguous()
+        ctx.check(ctx.lib.tc_orient_by(ctx.handle, n, m, _ptr(edges) if m else None, _ptr(keys), _ptr(offsets),
+                                       _ptr(cols), _ptr(deg), _ptr(dhat), _ptr(ws), ws.numel(), _stream(dev)))
     return Graph(n, m, offsets, cols[:m], deg[:n], dhat[:n])
 
 

@@ -279,7 +279,14 @@ tc_status tc_workspace_size(tc_op op, int32_t n, int64_t m, size_t* bytes) {
 
 tc_status tc_orient(tc_ctx* ctx, int32_t n, int64_t m, const int32_t* edges, int64_t* offsets, int32_t* cols,
                     int32_t* deg, int32_t* dhat, void* ws, size_t ws_bytes, tc_stream stream) {
+  return tc_orient_by(ctx, n, m, edges, nullptr, offsets, cols, deg, dhat, ws, ws_bytes, stream);
+}
+
+tc_status tc_orient_by(tc_ctx* ctx, int32_t n, int64_t m, const int32_t* edges, const int64_t* keys_dev,
+                       int64_t* offsets, int32_t* cols, int32_t* deg, int32_t* dhat, void* ws, size_t ws_bytes,
+                       tc_stream stream) {
   if (!ctx) return TC_ERR_INVALID_ARG;
+  if (keys_dev && !aligned(keys_dev, 8)) return fail(ctx, TC_ERR_INVALID_ARG, "keys not 8-byte aligned");
   if (n < 0 || m < 0) return fail(ctx, TC_ERR_INVALID_ARG, "negative n or m");
   if (!offsets || (n > 0 && (!deg || !dhat)) || (m > 0 && (!edges || !cols)))
     return fail(ctx, TC_ERR_INVALID_ARG, "NULL buffer");
@@ -291,7 +298,7 @@ tc_status tc_orient(tc_ctx* ctx, int32_t n, int64_t m, const int32_t* edges, int
   if ((st = begin(ctx, s)) != TC_OK) return st;
   Carver c(ws);
   tc::OrientWs w = tc::carve_orient(c, n, m);
-  return finish(ctx, s, tc::launch_orient(ctx, n, m, edges, offsets, cols, deg, dhat, w, s));
+  return finish(ctx, s, tc::launch_orient(ctx, n, m, edges, offsets, cols, deg, dhat, w, s, keys_dev));
 }
 
 static tc_status count_impl(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, int64_t* tv_dev, double* cc_dev,

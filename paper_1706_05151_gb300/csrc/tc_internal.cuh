@@ -186,8 +186,10 @@ cudaError_t exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, ScanW
                                const uint32_t* n_dev = nullptr);
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, ScanWs ws, cudaStream_t s);
 
+// keys: NULL for the degree order of Eq. (1), else v precedes u iff (keys[v], v) < (keys[u], u).
 cudaError_t launch_orient(Ctx* ctx, int32_t n, int64_t m, const int32_t* edges, int64_t* offsets,
-                          int32_t* cols, int32_t* deg, int32_t* dhat, OrientWs ws, cudaStream_t s);
+                          int32_t* cols, int32_t* deg, int32_t* dhat, OrientWs ws, cudaStream_t s,
+                          const int64_t* keys = nullptr);
 
 enum CountMode { MODE_COUNT = 0, MODE_LOCAL = 1, MODE_LIST_COUNT = 2, MODE_LIST_WRITE = 3 };
 

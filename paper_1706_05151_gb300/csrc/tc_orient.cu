@@ -1,7 +1,9 @@
 // Orientation by the degree order: the preprocessing of NodeIteratorN
 // (Figure 2): for each edge (u, v) store the later endpoint in the list of the
 // earlier one, where u precedes v iff d_u < d_v, or d_u = d_v and u < v
-// (Eq. (1)); then sort every list N_v ascending.
+// (Eq. (1)); then sort every list N_v ascending.  tc_orient_by replaces the
+// degree by a caller's key (any total order: Theorem 1 keeps T; Theorem 3 says
+// the degree order minimises sum_v d_v * dhat_v).
 //
 // GB300 mapping (all HBM/L2 traffic, no tensor cores):
 //   k_degree        grid-stride over the edge list, 8-byte pair loads, RED.ADD
@@ -33,8 +35,13 @@ OrientWs carve_orient(Carver& c, int32_t n, int64_t) {
 
 namespace {
 
-__device__ __forceinline__ bool precedes(int32_t da, int32_t a, int32_t db, int32_t b) {
+__device__ __forceinline__ bool precedes(int64_t da, int32_t a, int64_t db, int32_t b) {
   return da < db || (da == db && a < b);
+}
+
+// Order key of v: its degree (Eq. (1)), or the caller's key (tc_orient_by).
+__device__ __forceinline__ int64_t order_key(const int32_t* deg, const int64_t* keys, int32_t v) {
+  return keys ? keys[v] : static_cast<int64_t>(deg[v]);
 }
 
 __device__ __forceinline__ bool edge_ok(int2 p, int32_t n, uint32_t* err) {
@@ -96,7 +103,8 @@ __device__ __forceinline__ bool edge_valid(int2 p, int32_t n) {
 }
 
 __global__ void k_orient_count(const int2* __restrict__ edges, int64_t m, int32_t n,
-                               const int32_t* __restrict__ deg, int32_t* __restrict__ dhat) {
+                               const int32_t* __restrict__ deg, const int64_t* __restrict__ keys,
+                               int32_t* __restrict__ dhat) {
   FOR_EDGES(e, m) {
     const int64_t e = e0 + lane_id();
     int32_t src = 0;
@@ -104,7 +112,7 @@ __global__ void k_orient_count(const int2* __restrict__ edges, int64_t m, int32_
     if (e < m) {
       const int2 p = edges[e];
       ok = edge_valid(p, n);
-      if (ok) src = precedes(deg[p.x], p.x, deg[p.y], p.y) ? p.x : p.y;
+      if (ok) src = precedes(order_key(deg, keys, p.x), p.x, order_key(deg, keys, p.y), p.y) ? p.x : p.y;
     }
     int hl;
     const int c = run_length(src, ok, &hl);
@@ -113,7 +121,8 @@ __global__ void k_orient_count(const int2* __restrict__ edges, int64_t m, int32_
 }
 
 __global__ void k_scatter(const int2* __restrict__ edges, int64_t m, int32_t n, const int32_t* __restrict__ deg,
-                          const int64_t* __restrict__ offsets, int32_t* __restrict__ cursor,
+                          const int64_t* __restrict__ keys, const int64_t* __restrict__ offsets,
+                          int32_t* __restrict__ cursor,
                           int32_t* __restrict__ cols, uint32_t* err) {
   FOR_EDGES(e, m) {
     const int lane = lane_id();
@@ -124,7 +133,7 @@ __global__ void k_scatter(const int2* __restrict__ edges, int64_t m, int32_t n, 
       const int2 p = edges[e];
       ok = edge_valid(p, n);
       if (ok) {
-        const bool fwd = precedes(deg[p.x], p.x, deg[p.y], p.y);
+        const bool fwd = precedes(order_key(deg, keys, p.x), p.x, order_key(deg, keys, p.y), p.y);
         src = fwd ? p.x : p.y;
         dst = fwd ? p.y : p.x;
       }
@@ -257,6 +266,35 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_warp(const int64_t* __
   }
 }
 
+// One block sorts a list longer than its shared memory holds, in place in
+// global memory: bitonic sort in the form whose merges start by comparing each
+// element with its mirror in the block, so every comparator puts the smaller
+// key first and positions past the end act as +infinity without being stored.
+__device__ void sort_in_place(int32_t* a, int32_t len, uint32_t* err) {
+  int64_t P = 1;
+  while (P < len) P <<= 1;
+  for (int64_t k = 2; k <= P; k <<= 1) {
+    for (int64_t j = k >> 1; j > 0; j >>= 1) {
+      const int64_t mask = j == (k >> 1) ? k - 1 : j;  // first step of the merge: the mirror element
+      for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+        const int64_t l = i ^ mask;
+        if (l > i && l < len) {
+          const int32_t x = a[i], y = a[l];
+          if (x > y) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  bool dup = false;
+  for (int64_t i = threadIdx.x + 1; i < len; i += blockDim.x) dup |= a[i] == a[i - 1];
+  if (dup) set_err(err, ERR_DUPLICATE);
+  __syncthreads();
+}
+
 // One block per queued list (kSortWarpCap+1 .. kSortBlockCap ids): bitonic sort in shared memory.
 __global__ void __launch_bounds__(1024) k_sort_big(const int64_t* __restrict__ offsets, int32_t* __restrict__ cols,
                                                    const int32_t* __restrict__ big_queue,
@@ -267,8 +305,12 @@ __global__ void __launch_bounds__(1024) k_sort_big(const int64_t* __restrict__ o
     const int32_t v = big_queue[qi];
     const int64_t beg = offsets[v];
     const int64_t len = offsets[v + 1] - beg;
-    if (len > kSortBlockCap) {
-      if (threadIdx.x == 0) set_err(err, ERR_TOO_LONG);
+    if (len > kSortBlockCap) {  // only under other orders (tc_orient_by): sort in place in global memory
+      if (len > kMaxListLen) {
+        if (threadIdx.x == 0) set_err(err, ERR_TOO_LONG);
+        continue;
+      }
+      sort_in_place(cols + beg, static_cast<int32_t>(len), err);
       continue;
     }
     int P = 64;
@@ -306,7 +348,7 @@ bool g_big_attr_set[64] = {false};
 }  // namespace
 
 cudaError_t launch_orient(Ctx* ctx, int32_t n, int64_t m, const int32_t* edges, int64_t* offsets, int32_t* cols,
-                          int32_t* deg, int32_t* dhat, OrientWs ws, cudaStream_t s) {
+                          int32_t* deg, int32_t* dhat, OrientWs ws, cudaStream_t s, const int64_t* keys) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(deg, 0, sizeof(int32_t) * static_cast<size_t>(n), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(dhat, 0, sizeof(int32_t) * static_cast<size_t>(n), s)) != cudaSuccess) return e;
@@ -322,7 +364,7 @@ cudaError_t launch_orient(Ctx* ctx, int32_t n, int64_t m, const int32_t* edges, 
     }
     {
       Stage st(ctx, s, "orient.orient_count");
-      k_orient_count<<<grid_e, threads, 0, s>>>(ep, m, n, deg, dhat);
+      k_orient_count<<<grid_e, threads, 0, s>>>(ep, m, n, deg, keys, dhat);
     }
     counted(ctx, 2);
   }
@@ -333,7 +375,7 @@ cudaError_t launch_orient(Ctx* ctx, int32_t n, int64_t m, const int32_t* edges, 
   }
   if (m > 0) {
     Stage st(ctx, s, "orient.scatter");
-    k_scatter<<<grid_e, threads, 0, s>>>(ep, m, n, deg, offsets, ws.cursor, cols, ctx->d_err);
+    k_scatter<<<grid_e, threads, 0, s>>>(ep, m, n, deg, keys, offsets, ws.cursor, cols, ctx->d_err);
     counted(ctx);
   }
   if (n > 0) {
