@@ -339,6 +339,31 @@ def bench_orders(tc, ctx, edges_dev, n, T, dev, seed):
     return out
 
 
+def bench_sparsify_accuracy(tc, ctx, g, T, dev, q, seeds: int = 25, parts: int = 8):
+    """Section 9.2's accuracy comparison on this graph: the estimate T'/q^3 over
+    `seeds` independent runs, with one coin per edge (DOULION) and with
+    partition-local coins (each of `parts` work-balanced parts draws its own)."""
+    import torch
+    b, _ = tc.partition(g, parts, tc.COST_WORK, ctx)
+    b = b.cpu().numpy()
+    plain, parted = [], []
+    for s in range(seeds):
+        t, _, _ = tc.sparsify_count(g, q, 1000 + s, ctx)
+        plain.append(t / q ** 3)
+        kept = torch.zeros(1, dtype=torch.int64, device=dev)
+        for j in range(parts):
+            tc.sparsify_count_part(g, q, 1000 + s, j, int(b[j]), int(b[j + 1]), kept, ctx)
+        parted.append(int(kept.item()) / q ** 3)
+
+    def stats(x):
+        x = np.array(x)
+        err = np.abs(x - T) / T if T else np.zeros_like(x)
+        return {"mean_estimate": float(x.mean()), "variance": float(x.var(ddof=1)),
+                "mean_rel_error": float(err.mean()), "max_rel_error": float(err.max())}
+    return {"q": q, "seeds": seeds, "parts": parts, "T": T, "one_coin_per_edge": stats(plain),
+            "partition_local_coins": stats(parted)}
+
+
 def serving_pool():
     """The serving configuration's graph pool (seeded): ER n = 2^12..2^18 with mean
     degree 16, R-MAT scale 16..20 with edge factor 16, Chung-Lu (gamma 2.1) with
@@ -496,6 +521,8 @@ def main():
                     help="skip the load-balancing partition report")
     ap.add_argument("--no-orders", dest="orders", action="store_false",
                     help="skip the node-ordering report (id, degree, random orders)")
+    ap.add_argument("--no-sparsify-study", dest="sparsify_study", action="store_false",
+                    help="skip the 25-seed sparsification accuracy report")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -599,6 +626,7 @@ def main():
 
     part = bench_partition(tc, ctx, g, T, dev) if world == 1 and args.partition else None
     orders = bench_orders(tc, ctx, edges_dev, n, T, dev, args.seed) if world == 1 and args.orders else None
+    spacc = bench_sparsify_accuracy(tc, ctx, g, T, dev, q) if world == 1 and args.sparsify_study else None
 
     batched = None
     if args.batch_graphs > 0:
@@ -655,6 +683,7 @@ def main():
             "cpu_baseline": cpu,
             "partition": part,
             "orders": orders,
+            "sparsify_accuracy": spacc,
             "batched": batched,
             "serving": serving,
             "sparsified": {"kept_edges": sp[1], "kept_triangles": sp[0], "estimate": sp[2],

@@ -260,6 +260,24 @@ tc_status tc_sparsify_count(tc_ctx* ctx, const tc_graph* g, double q, uint64_t s
                             uint64_t* kept_tri_dev, int64_t* kept_edges_dev, void* ws, size_t ws_bytes,
                             tc_stream stream);
 
+/*
+ * Sparsification with partition-local coins (Section 9.2: each processor
+ * sparsifies the partition it loads, Figure "sparsification"): the triangles
+ * whose apex (first vertex in the order of Eq. (1)) lies in [v_begin, v_end),
+ * counted on the graph in which this part keeps each edge with probability q
+ * by its own coin -- Philox4x64-10 with counter (min(a,b), max(a,b), part, 0)
+ * and key (seed, 0), keep iff (w0 >> 11) < ceil(q * 2^53).  part = 0 draws the
+ * coins of tc_sparsify_count.  Run over the parts of a partition, each with its
+ * own index, sum T'/q^3 is unbiased, and two triangles of different parts that
+ * share an edge survive independently, so the variance is Eq. var2's (k' <= k).
+ *   kept_tri_dev   device uint64[1]: ADDS this part's kept triangles
+ *   kept_edges_dev device int64[1]: overwritten with the edges this part's coins keep
+ * Workspace: tc_workspace_size(TC_OP_SPARSIFY, n, m).
+ */
+tc_status tc_sparsify_count_part(tc_ctx* ctx, const tc_graph* g, double q, uint64_t seed, int32_t part,
+                                 int32_t v_begin, int32_t v_end, uint64_t* kept_tri_dev, int64_t* kept_edges_dev,
+                                 void* ws, size_t ws_bytes, tc_stream stream);
+
 /* ---- cost-balanced partition of the apex vertices (Section "load balancing") --- */
 
 /*

@@ -74,6 +74,9 @@ def _load():
         lib.orc_philox.argtypes = [u64p, u64p, u64p]
         lib.orc_sparsify_keep.restype = ctypes.c_int
         lib.orc_sparsify_keep.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double]
+        lib.orc_sparsify_keep_part.restype = ctypes.c_int
+        lib.orc_sparsify_keep_part.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double,
+                                               ctypes.c_uint64]
         lib.orc_sparsify_count.restype = ctypes.c_int
         lib.orc_sparsify_count.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, ctypes.c_uint64,
                                            ctypes.c_double, u64p, i64p, f64p]
@@ -272,3 +275,23 @@ def count_apex_range(n: int, edges, lo: int, hi: int):
     sel = tri[(tri[:, 0] >= lo) & (tri[:, 0] < hi)]
     tv = np.bincount(sel.ravel(), minlength=n).astype(np.int64) if len(sel) else np.zeros(n, np.int64)
     return int(len(sel)), tv
+
+
+# ---- sparsification with partition-local coins (Section 9.2) ----
+
+def sparsify_keep_part(a: int, b: int, seed: int, q: float, part: int) -> bool:
+    """The coin of edge {a, b} drawn by part `part`: Philox4x64-10 with counter
+    (min, max, part, 0) and key (seed, 0); kept iff (w0 >> 11) * 2^-53 < q."""
+    return bool(_load().orc_sparsify_keep_part(int(a), int(b), int(seed), float(q), int(part)))
+
+
+def sparsify_count_part(n: int, edges, seed: int, q: float, part: int, lo: int, hi: int) -> int:
+    """Figure "sparsification" run by one processor on its partition: the part keeps
+    each edge by its own coin, and counts the triangles of the kept graph whose first
+    vertex -- in the order of the ORIGINAL degrees -- lies in [lo, hi)."""
+    e = _edges(edges)
+    deg = Adjacency(n, e).deg.astype(np.int64)
+    kept = np.array([p for p in e if sparsify_keep_part(int(p[0]), int(p[1]), seed, q, part)],
+                    dtype=np.int32).reshape(-1, 2)
+    tri = count(n, kept, order_key=deg, listing=True)["tri"]
+    return int(((tri[:, 0] >= lo) & (tri[:, 0] < hi)).sum())

@@ -271,13 +271,24 @@ void orc_philox(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
   orc_philox4x64_10(ctr, key, out);
 }
 
+int orc_sparsify_keep_part(int32_t a, int32_t b, uint64_t seed, double q, uint64_t part);
+
 /*
  * The sparsification coin of Section 9.1: edge {a, b} is retained with
  * probability q, independently of the others, and the coin depends only on
  * the edge (not on any storage order).
  */
 int orc_sparsify_keep(int32_t a, int32_t b, uint64_t seed, double q) {
-  uint64_t ctr[4] = {(uint64_t)(a < b ? a : b), (uint64_t)(a < b ? b : a), 0, 0};
+  return orc_sparsify_keep_part(a, b, seed, q, 0);
+}
+
+/*
+ * The coin of edge {a, b} drawn by processor `part` when it sparsifies the
+ * partition it loads (Section 9.2): the same generator with the part's index
+ * as the third counter word; part 0 is the coin above.
+ */
+int orc_sparsify_keep_part(int32_t a, int32_t b, uint64_t seed, double q, uint64_t part) {
+  uint64_t ctr[4] = {(uint64_t)(a < b ? a : b), (uint64_t)(a < b ? b : a), part, 0};
   uint64_t key[2] = {seed, 0};
   uint64_t out[4];
   orc_philox4x64_10(ctr, key, out);

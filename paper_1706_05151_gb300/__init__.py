@@ -41,7 +41,8 @@ EXPORTS = ["tc_ctx_create", "tc_ctx_destroy", "tc_ctx_set_async", "tc_ctx_status
            "tc_serve_stats",
            "tc_ctx_set_tuning", "tc_ctx_set_hub_min", "tc_ctx_set_profiling", "tc_ctx_stage_count", "tc_ctx_stage", "tc_ctx_reset_stats", "tc_ctx_launches",
            "tc_count_static", "tc_capture_begin", "tc_capture_end", "tc_exec_launch", "tc_exec_kernels",
-           "tc_exec_destroy", "tc_partition", "tc_count_range", "tc_orient_by"]
+           "tc_exec_destroy", "tc_partition", "tc_count_range", "tc_orient_by",
+           "tc_sparsify_count_part"]
 
 
 class TcError(RuntimeError):
@@ -110,6 +111,7 @@ def load_library(path: str = LIB_PATH):
             "tc_analyze": (i32, [vp, G, vp, vp, vp, vp, i64, ctypes.POINTER(i64), vp, sz, vp]),
             "tc_batch": (i32, [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
             "tc_orient_by": (i32, [vp, i32, i64, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+            "tc_sparsify_count_part": (i32, [vp, G, ctypes.c_double, u64, i32, i32, i32, vp, vp, vp, sz, vp]),
             "tc_partition": (i32, [vp, G, i32, ctypes.c_int, vp, vp, vp, sz, vp]),
             "tc_count_range": (i32, [vp, G, i32, i32, vp, vp, vp, sz, vp]),
             "tc_capture_begin": (i32, [vp, vp]),
@@ -372,6 +374,19 @@ def sparsify_count(g: Graph, q: float, seed: int, ctx: Context | None = None):
     t = int(kept_tri.item())
     est = float(t) / (q * q * q) if q > 0 else float("nan")
     return t, int(kept_edges.item()), est
+
+
+def sparsify_count_part(g: Graph, q: float, seed: int, part: int, v_begin: int, v_end: int,
+                        kept: torch.Tensor, ctx: Context | None = None) -> int:
+    """tc_sparsify_count_part: ADD to kept (int64[1]) the triangles with apex in [v_begin, v_end)
+    that survive this part's own coins; returns the number of edges those coins keep."""
+    ctx = ctx or default_context()
+    kept_edges = torch.zeros(1, dtype=torch.int64, device=ctx.device)
+    ws = ctx.workspace(TC_OP_SPARSIFY, g.n, g.m)
+    ctx.check(ctx.lib.tc_sparsify_count_part(ctx.handle, ctypes.byref(g.struct()), float(q), int(seed), int(part),
+                                             int(v_begin), int(v_end), _ptr(kept), _ptr(kept_edges), _ptr(ws),
+                                             ws.numel(), _stream(ctx.device)))
+    return int(kept_edges.item())
 
 
 def partition(g: Graph, parts: int, cost: int = COST_WORK, ctx: Context | None = None):

@@ -506,6 +506,34 @@ tc_status tc_batch(tc_ctx* ctx, int32_t G, int32_t N, int64_t E, const int64_t* 
   return finish(ctx, s, e);
 }
 
+tc_status tc_sparsify_count_part(tc_ctx* ctx, const tc_graph* g, double q, uint64_t seed, int32_t part,
+                                 int32_t v_begin, int32_t v_end, uint64_t* kept_tri_dev, int64_t* kept_edges_dev,
+                                 void* ws, size_t ws_bytes, tc_stream stream) {
+  tc_status st = check_graph(ctx, g);
+  if (st != TC_OK) return st;
+  if (!(q >= 0.0 && q <= 1.0)) return fail(ctx, TC_ERR_INVALID_ARG, "q must be in [0, 1]");
+  if (part < 0) return fail(ctx, TC_ERR_INVALID_ARG, "part must be >= 0");
+  if (v_begin < 0 || v_end < v_begin || v_end > g->n)
+    return fail(ctx, TC_ERR_INVALID_ARG, "need 0 <= v_begin <= v_end <= n");
+  if (!kept_tri_dev || !kept_edges_dev) return fail(ctx, TC_ERR_INVALID_ARG, "NULL output");
+  if ((st = check_ws(ctx, TC_OP_SPARSIFY, g->n, g->m, ws, ws_bytes)) != TC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = begin(ctx, s)) != TC_OK) return st;
+  Carver c(ws);
+  tc::SparsifyWs w = tc::carve_sparsify(c, g->n, g->m);
+  const uint64_t t53 = static_cast<uint64_t>(std::ceil(q * 9007199254740992.0));
+  cudaError_t e = tc::launch_sparsify(ctx, g->n, g->m, g->offsets, g->cols, t53, seed, static_cast<uint64_t>(part), w,
+                                      kept_edges_dev, s);
+  if (e == cudaSuccess && v_end > v_begin) {
+    tc::CountArgs a{g->n, g->m, w.offsets, w.cols, reinterpret_cast<unsigned long long*>(kept_tri_dev), nullptr,
+                    nullptr, 0};
+    a.v_lo = v_begin;
+    a.v_hi = v_end;
+    e = tc::launch_count(ctx, tc::MODE_COUNT, a, w.count, s);
+  }
+  return finish(ctx, s, e);
+}
+
 tc_status tc_sparsify_count(tc_ctx* ctx, const tc_graph* g, double q, uint64_t seed, uint64_t* kept_tri_dev,
                             int64_t* kept_edges_dev, void* ws, size_t ws_bytes, tc_stream stream) {
   tc_status st = check_graph(ctx, g);
@@ -521,7 +549,7 @@ tc_status tc_sparsify_count(tc_ctx* ctx, const tc_graph* g, double q, uint64_t s
   const uint64_t t53 = static_cast<uint64_t>(std::ceil(q * 9007199254740992.0));
   cudaError_t e = cudaMemsetAsync(kept_tri_dev, 0, sizeof(uint64_t), s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "clear outputs");
-  e = tc::launch_sparsify(ctx, g->n, g->m, g->offsets, g->cols, t53, seed, w, kept_edges_dev, s);
+  e = tc::launch_sparsify(ctx, g->n, g->m, g->offsets, g->cols, t53, seed, 0, w, kept_edges_dev, s);
   if (e == cudaSuccess) {
     tc::CountArgs a{g->n, g->m, w.offsets, w.cols, reinterpret_cast<unsigned long long*>(kept_tri_dev), nullptr,
                     nullptr, 0};

@@ -6,7 +6,9 @@
 // The coin of undirected edge {a, b} depends only on the edge:
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) with counter
 // (min(a,b), max(a,b), 0, 0) and key (seed, 0); keep iff (w0 >> 11) < t53,
-// where t53 = ceil(q * 2^53) is computed on the host.
+// where t53 = ceil(q * 2^53) is computed on the host.  With partition-local
+// coins (Section 9.2, tc_sparsify_count_part) the third counter word is the
+// part's index, so each part draws its own coin for every edge it holds.
 //
 // GB300 mapping: a warp takes 32 consecutive vertices, whose lists are one
 // contiguous run of cols; lanes walk that run 32 ids at a time (coalesced), and
@@ -94,7 +96,7 @@ constexpr int kSpWarps = 8;
 
 __global__ void __launch_bounds__(kSpWarps * 32) k_mark(int32_t n, int64_t m, const int64_t* __restrict__ off,
                                                         const int32_t* __restrict__ cols, uint64_t t53,
-                                                        uint64_t seed, uint8_t* __restrict__ keep,
+                                                        uint64_t seed, uint64_t part, uint8_t* __restrict__ keep,
                                                         int32_t* __restrict__ kept_count, uint32_t* err) {
   __shared__ int64_t s_beg[kSpWarps][32];
   __shared__ int32_t s_cnt[kSpWarps][32];
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(kSpWarps * 32) k_mark(int32_t n, int64_t m, co
       const int s = owner(s_beg[wid], idx);
       const uint64_t v = static_cast<uint64_t>(vb + s);
       const uint64_t u = static_cast<uint64_t>(static_cast<uint32_t>(cols[idx]));
-      const uint64_t w0 = philox4x64_10_w0(v < u ? v : u, v < u ? u : v, 0, 0, seed, 0);
+      const uint64_t w0 = philox4x64_10_w0(v < u ? v : u, v < u ? u : v, part, 0, seed, 0);
       const bool k = (w0 >> 11) < t53;
       keep[idx] = k ? 1 : 0;
       if (k) atomicAdd(&s_cnt[wid][s], 1);
@@ -169,13 +171,13 @@ __global__ void k_copy_last(const int64_t* __restrict__ new_off, int32_t n, int6
 }  // namespace
 
 cudaError_t launch_sparsify(Ctx* ctx, int32_t n, int64_t m, const int64_t* offsets, const int32_t* cols,
-                            uint64_t threshold53, uint64_t seed, SparsifyWs ws, int64_t* kept_edges,
+                            uint64_t threshold53, uint64_t seed, uint64_t part, SparsifyWs ws, int64_t* kept_edges,
                             cudaStream_t s) {
   cudaError_t e;
   if (n > 0) {
     const int grid = persistent_blocks(ctx, reinterpret_cast<const void*>(&k_mark), kSpWarps * 32, 0);
     Stage st(ctx, s, "sparsify.mark");
-    k_mark<<<grid, kSpWarps * 32, 0, s>>>(n, m, offsets, cols, threshold53, seed, ws.keep, ws.kept_count,
+    k_mark<<<grid, kSpWarps * 32, 0, s>>>(n, m, offsets, cols, threshold53, seed, part, ws.keep, ws.kept_count,
                                           ctx->d_err);
     counted(ctx);
   }

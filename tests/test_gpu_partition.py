@@ -100,3 +100,22 @@ def test_range_and_partition_errors(tc):
         with pytest.raises(tc.TcError):
             tc.partition(g, parts, cost)
     assert int(T.item()) == 0
+
+
+def test_partition_local_sparsification_matches_oracle(tc):
+    for name, n, e in graphs()[:4]:
+        g = tc.orient(to_dev(synth.shuffle_edges(e, 2)), n)
+        b, _ = tc.partition(g, 4, tc.COST_WORK)
+        b = b.cpu().numpy()
+        for seed, q in ((1, 0.3), (7, 0.1)):
+            kept = torch.zeros(1, dtype=torch.int64, device="cuda")
+            for j in range(4):
+                before = int(kept.item())
+                tc.sparsify_count_part(g, q, seed, j, int(b[j]), int(b[j + 1]), kept)
+                ref = oracle.sparsify_count_part(n, e, seed, q, j, int(b[j]), int(b[j + 1]))
+                assert int(kept.item()) - before == ref, (name, seed, j)
+        # part 0 over every apex is tc_sparsify_count
+        kept = torch.zeros(1, dtype=torch.int64, device="cuda")
+        mk = tc.sparsify_count_part(g, 0.2, 5, 0, 0, n, kept)
+        t, mk2, _ = tc.sparsify_count(g, 0.2, 5)
+        assert (int(kept.item()), mk) == (t, mk2)

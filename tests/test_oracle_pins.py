@@ -386,3 +386,50 @@ def test_apex_ranges_sum_to_the_whole():
         tv += t
     assert total == ref["T"]
     assert np.array_equal(tv, ref["tv"])
+
+
+# ---- sparsification with partition-local coins (Section 9.2, Eq. var2) ----
+
+def test_part_coin_reduces_to_the_plain_coin_and_to_philox():
+    rng = np.random.default_rng(1)
+    for _ in range(300):
+        a, b = (int(x) for x in rng.integers(0, 1 << 20, 2))
+        seed, q = int(rng.integers(0, 1 << 40)), float(rng.random())
+        assert oracle.sparsify_keep_part(a, b, seed, q, 0) == oracle.sparsify_keep(a, b, seed, q)
+        part = int(rng.integers(0, 64))
+        w0 = int(oracle.philox([min(a, b), max(a, b), part, 0], [seed, 0])[0])
+        assert oracle.sparsify_keep_part(a, b, seed, q, part) == ((w0 >> 11) * 2.0 ** -53 < q)
+
+
+def test_parts_with_q_one_sum_to_t():
+    n, e = 256, synth.rmat(8, 8, 2)
+    b, _ = oracle.partition(n, e, 4, oracle.COST_WORK)
+    total = sum(oracle.sparsify_count_part(n, e, 3, 1.0, j, int(b[j]), int(b[j + 1])) for j in range(4))
+    assert total == oracle.count(n, e)["T"]
+
+
+def test_partitioned_estimator_unbiased_with_var2():
+    # parts sparsify independently: E[sum T'_j / q^3] = T and
+    # Var' = (1/q^3 - 1) T + 2 k' (1/q - 1), k' = pairs of triangles sharing an edge
+    # with both apexes (first vertices in the order of Eq. (1)) in the same part (Eq. var2)
+    n = 200
+    e = synth.ba(n, 6, 21)
+    deg = oracle.Adjacency(n, e).deg
+    parts = 4
+    bounds, _ = oracle.partition(n, e, parts, oracle.COST_WORK)
+    tris = brute.triangles_by_neighbours(n, e)
+    T = len(tris)
+    part_of = np.searchsorted(bounds, np.arange(n), side="right") - 1
+    apex = [min(t, key=lambda x: (deg[x], x)) for t in tris]
+    k_same = 0
+    for j in range(parts):
+        k_same += brute.edge_triangle_pairs([t for t, a in zip(tris, apex) if part_of[a] == j])
+    k_all = brute.edge_triangle_pairs(tris)
+    assert k_same < k_all  # the partition separates some pairs: var2 < var1 here
+    q = 0.5
+    var2 = (1 / q ** 3 - 1) * T + 2 * k_same * (1 / q - 1)
+    S = 240
+    ests = np.array([sum(oracle.sparsify_count_part(n, e, s, q, j, int(bounds[j]), int(bounds[j + 1]))
+                         for j in range(parts)) / q ** 3 for s in range(S)])
+    assert abs(ests.mean() - T) < 4.5 * math.sqrt(var2 / S)
+    assert 0.65 * var2 < ests.var(ddof=1) < 1.45 * var2
