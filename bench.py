@@ -364,6 +364,27 @@ def bench_sparsify_accuracy(tc, ctx, g, T, dev, q, seeds: int = 25, parts: int =
             "partition_local_coins": stats(parted)}
 
 
+def bench_host_resident(tc, ctx, g, T, dev):
+    """The count with the oriented CSR in page-locked host memory, read by the kernels
+    over the CPU-GPU link (graphs that do not fit in the device memory left free)."""
+    import torch
+    h = tc.Graph(g.n, g.m, g.offsets.cpu().pin_memory(), g.cols.cpu().pin_memory(), g.deg.cpu().pin_memory(),
+                 g.dhat.cpu().pin_memory())
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty(1, dtype=torch.int64, device=dev)
+    tc.count(h, ctx, out=out)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        tc.count(h, ctx, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / 3
+    return {"count_ms": round(ms, 3), "edges_per_s": g.m / (ms * 1e-3), "triangles_equal": int(out.item()) == T,
+            "csr_bytes": 8 * (g.n + 1) + 4 * g.m + 8 * g.n}
+
+
 def serving_pool():
     """The serving configuration's graph pool (seeded): ER n = 2^12..2^18 with mean
     degree 16, R-MAT scale 16..20 with edge factor 16, Chung-Lu (gamma 2.1) with
@@ -523,6 +544,8 @@ def main():
                     help="skip the node-ordering report (id, degree, random orders)")
     ap.add_argument("--no-sparsify-study", dest="sparsify_study", action="store_false",
                     help="skip the 25-seed sparsification accuracy report")
+    ap.add_argument("--no-host-study", dest="host_study", action="store_false",
+                    help="skip the count with the CSR in host memory")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -627,6 +650,7 @@ def main():
     part = bench_partition(tc, ctx, g, T, dev) if world == 1 and args.partition else None
     orders = bench_orders(tc, ctx, edges_dev, n, T, dev, args.seed) if world == 1 and args.orders else None
     spacc = bench_sparsify_accuracy(tc, ctx, g, T, dev, q) if world == 1 and args.sparsify_study else None
+    host = bench_host_resident(tc, ctx, g, T, dev) if world == 1 and args.host_study else None
 
     batched = None
     if args.batch_graphs > 0:
@@ -684,6 +708,7 @@ def main():
             "partition": part,
             "orders": orders,
             "sparsify_accuracy": spacc,
+            "host_resident_csr": host,
             "batched": batched,
             "serving": serving,
             "sparsified": {"kept_edges": sp[1], "kept_triangles": sp[0], "estimate": sp[2],

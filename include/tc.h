@@ -77,7 +77,10 @@ typedef void* tc_stream; /* cudaStream_t */
  * The counting calls need only a CSR whose lists are sorted, strictly
  * increasing and form an acyclic orientation; they check offsets and ids
  * against n and m and report TC_ERR_INVALID_GRAPH instead of reading out of
- * bounds.
+ * bounds.  The four arrays may also live in host memory the GPU can address
+ * (page-locked memory, or system memory on a coherent CPU-GPU node): the
+ * kernels then read the graph over the CPU-GPU link, for graphs larger than
+ * the device memory left free (outputs and workspace stay on the device).
  */
 typedef struct {
   int32_t n;

@@ -14,17 +14,22 @@
 //                  than tile_max are queued for k_count_block).  The tile's
 //                  oriented edges (v, u) are processed 32 at a time.  Short
 //                  lists N_u are laid end to end and walked in 32-wide windows
-//                  (an owner table maps a position to its edge), kUnroll
-//                  windows at once so each lane has kUnroll independent global
-//                  loads in flight; long lists are walked one edge at a time.
-//                  Every candidate w first meets a bitmap filter of the tile
-//                  (one shared load and a bit test); the survivors are queued
-//                  and checked exactly, 32 at a time, by binary search in N_v's
-//                  slice of the tile.
-//   k_count_block  one block per queued vertex: N_v is hashed into a shared-
-//                  memory open-addressing table (load factor at most 1/4), so
-//                  membership is exact in about one probe; the block's warps
-//                  share the out-neighbour batches.
+//                  (an owner table maps a position to its edge), kTileUnroll
+//                  windows at once so each lane has that many independent
+//                  global loads in flight; long lists are walked one edge at a
+//                  time.  Every candidate w first meets a bitmap filter of the
+//                  tile (one shared load and a bit test); the survivors are
+//                  queued and checked exactly, 32 at a time, by binary search
+//                  in N_v's slice of the tile.
+//   k_count_block  one block per queued vertex: N_v is hashed, in chunks, into
+//                  a shared-memory two-choice (cuckoo) table at load factor at
+//                  most 1/4, so membership is exact in two independent loads;
+//                  the block's warps take the out-neighbour batches in turn.
+//   hub side       an edge (v, u) whose N_u is long (>= hub_min ids) and longer
+//                  than N_v is counted from u's side: k_count_block<MODE, true>
+//                  hashes N_u once per segment of such edges and streams the
+//                  short N_v lists (k_hub_list / k_hub_fill / k_hub_items build
+//                  the segments).
 // Counts are summed per edge and per vertex in shared memory, per warp by
 // shuffles and per block by one 64-bit atomicAdd.
 //

@@ -325,3 +325,16 @@ def test_listing_of_lists_longer_than_one_hash_chunk(tc):
     assert bool(torch.all(key[1:] > key[:-1]))  # all distinct, so all C(n, 3) present
     del key
     assert torch.equal(tc.list_triangles(g), tri)
+
+
+def test_csr_in_host_memory(tc):
+    """A CSR held in page-locked host memory is read over the CPU-GPU link: same results."""
+    n, e = 1 << 14, synth.rmat(14, 16, 21)
+    g = tc.orient(to_dev(e), n)
+    T, tv, cc = tc.count_local(g)
+    h = tc.Graph(n, g.m, g.offsets.cpu().pin_memory(), g.cols.cpu().pin_memory(), g.deg.cpu().pin_memory(),
+                 g.dhat.cpu().pin_memory())
+    T2, tv2, cc2 = tc.count_local(h)
+    assert T2 == T
+    assert torch.equal(tv2, tv) and torch.equal(cc2, cc)
+    assert tc.count(h) == T
