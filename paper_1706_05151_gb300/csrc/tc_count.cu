@@ -53,6 +53,7 @@ constexpr int kShortLen = 32;        // N_u shorter than this is walked end to e
 constexpr int kOwnCap = 32 * kShortLen;
 constexpr int kTileUnroll = 8;       // candidate windows in flight per lane, tile kernel
 constexpr int kBlockWarps = 8;       // warps per block, block kernel
+constexpr int kHashBatch = 32;       // walked lists a warp takes at a time (block and hub kernels, <= 32)
 constexpr int64_t kBegBias = 1024;   // beg >= -(32 * kShortLen): biased to stay non-negative when packed
 constexpr uint64_t kBegMask = (uint64_t(1) << 58) - 1;
 constexpr int kHubMinDefault = 64;   // default hub_min: lists of at least this many ids take their in-edges
@@ -789,10 +790,11 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
       const int32_t lo = a.cols[b + c0], hi = a.cols[b + c0 + clen - 1];
       for (;;) {
         int64_t ub = 0;
-        if (lane == 0) ub = atomicAdd(reinterpret_cast<unsigned long long*>(&s_next), 32ull);
+        if (lane == 0) ub = atomicAdd(reinterpret_cast<unsigned long long*>(&s_next),
+                                      static_cast<unsigned long long>(kHashBatch));
         ub = __shfl_sync(FULL, ub, 0);
         if (ub >= nl) break;
-        const int nb = static_cast<int>(min64(32, nl - ub));
+        const int nb = static_cast<int>(min64(kHashBatch, nl - ub));
         bool act = lane < nb;
         int32_t x = 0;
         int64_t eg = 0;
