@@ -193,7 +193,7 @@ def bench_batched(tc, ctx, dev, args, rank):
     import ctypes
     import torch
     import synth
-    graphs = synth.batch_graphs(args.batch_graphs, 4096 + args.seed + rank)
+    graphs = synth.batch_graphs(args.batch_graphs, 4096 + replica_seed(args.seed, rank))
     b = tc.make_batch(graphs, dev)
     G, N, E = b.G, b.N, b.E
     stream = torch.cuda.current_stream(dev)
@@ -480,6 +480,40 @@ def bench_serving(tc, dev, args):
     return out
 
 
+# ---- replicas on several GPUs (one process per GPU; no collective on the data path) ----
+
+def replica_seed(seed: int, rank: int) -> int:
+    """Each rank counts its own independent graph of the same workload."""
+    return seed + rank
+
+
+def max_over_ranks(x: float, device, world: int) -> float:
+    """The slowest rank's time (the job's time): an all-reduce MAX, or x alone."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: int, device, world: int) -> int:
+    """Units processed by the whole job: an all-reduce SUM, or x alone."""
+    if world <= 1:
+        return int(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([int(x)], dtype=torch.int64, device=device)
+    dist.all_reduce(t)
+    return int(t.item())
+
+
+def job_throughput(units_all_ranks: int, ms_slowest: float) -> float:
+    """value: every rank's units over the slowest rank's time."""
+    return units_all_ranks / (ms_slowest * 1e-3)
+
+
 def run_e2e(args, tc, ctx, dev, edges_host, n, T, q, seed, tri_buf, barrier, world):
     """The step end to end through the public API: H2D of the edge list and D2H of
     T_v, C_v and the listing inside the timed region.  Returns ms per step (max over ranks)."""
@@ -510,11 +544,7 @@ def run_e2e(args, tc, ctx, dev, edges_host, n, T, q, seed, tri_buf, barrier, wor
     e1.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    return e2e_ms
+    return max_over_ranks(e2e_ms, dev, world)
 
 
 def main():
@@ -569,7 +599,7 @@ def main():
         dist.barrier()
     ctx = tc.Context(local_rank)
     w = WORKLOADS[args.workload]
-    n, e_np = make_graph(w, args.seed + rank)
+    n, e_np = make_graph(w, replica_seed(args.seed, rank))
     m = len(e_np)
     edges_host = torch.from_numpy(e_np).pin_memory()
     edges_dev = edges_host.to(dev)
@@ -628,11 +658,7 @@ def main():
     ctx.set_profiling(False)
     launches = ctx.launches
     stages = ctx.stages()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dev, world)
     sampler.mark(t_wall0, t_wall1)
     clocks = sampler.stop()
 
@@ -640,12 +666,7 @@ def main():
     e2e_ms = None
     if args.e2e_steps > 0:
         e2e_ms = run_e2e(args, tc, ctx, dev, edges_host, n, T, q, seed, tri_buf, barrier, world)
-    if world > 1:
-        mt = torch.tensor([m], device=dev, dtype=torch.int64)
-        dist.all_reduce(mt)
-        m_total = int(mt.item())
-    else:
-        m_total = m
+    m_total = sum_over_ranks(m, dev, world)
 
     part = bench_partition(tc, ctx, g, T, dev) if world == 1 and args.partition else None
     orders = bench_orders(tc, ctx, edges_dev, n, T, dev, args.seed) if world == 1 and args.orders else None
@@ -685,7 +706,7 @@ def main():
         h2d = 8 * m
         d2h = 16 * n + 12 * T + 8 * 3
         out = {
-            "metric": METRIC, "value": m_total / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": job_throughput(m_total, ms), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": w["label"], "n": n, "m": m, "triangles": T, "W_sum_d_dhat": W,
@@ -699,7 +720,7 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_count_tile+k_count_block+hub side, per-vertex pass of tc_analyze",
                          "algorithmic_bytes": b_alg, "avg_launch_ms": inter_avg_ms, "peak_source": peak_src},
-            "e2e": ({"value": m_total / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": ({"value": job_throughput(m_total, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                      "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms} if e2e_ms else None),
             "gpu_launches": launches,
             "clocks": clocks,
