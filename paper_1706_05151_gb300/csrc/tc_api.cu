@@ -392,8 +392,9 @@ tc_status tc_list_count(tc_ctx* ctx, const tc_graph* g, int64_t* total_dev, void
   return finish(ctx, s, e);
 }
 
-tc_status tc_list_write(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_t cap, void* ws, size_t ws_bytes,
-                        tc_stream stream) {
+// The write pass; reuse_hub when the counting pass on the same workspace ran just before (same call).
+static tc_status list_write_impl(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_t cap, void* ws, size_t ws_bytes,
+                          tc_stream stream, bool reuse_hub) {
   tc_status st = check_graph(ctx, g);
   if (st != TC_OK) return st;
   if (cap < 0 || (cap > 0 && !tri_dev)) return fail(ctx, TC_ERR_INVALID_ARG, "bad output buffer");
@@ -403,7 +404,13 @@ tc_status tc_list_write(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_
   Carver c(ws);
   tc::CountWs w = tc::carve_count(c, g->n, g->m, true);
   tc::CountArgs a{g->n, g->m, g->offsets, g->cols, nullptr, nullptr, tri_dev, cap};
+  a.reuse_hub = reuse_hub;
   return finish(ctx, s, tc::launch_count(ctx, tc::MODE_LIST_WRITE, a, w, s));
+}
+
+tc_status tc_list_write(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_t cap, void* ws, size_t ws_bytes,
+                        tc_stream stream) {
+  return list_write_impl(ctx, g, tri_dev, cap, ws, ws_bytes, stream, false);
 }
 
 tc_status tc_list(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_t cap, int64_t* count_out, void* ws,
@@ -431,7 +438,7 @@ tc_status tc_list(tc_ctx* ctx, const tc_graph* g, int32_t* tri_dev, int64_t cap,
   *count_out = total;
   if (total > cap) return fail(ctx, TC_ERR_CAPACITY, "listing needs %lld triples, capacity %lld",
                                static_cast<long long>(total), static_cast<long long>(cap));
-  return tc_list_write(ctx, g, tri_dev, cap, ws, ws_bytes, stream);
+  return list_write_impl(ctx, g, tri_dev, cap, ws, ws_bytes, stream, true);
 }
 
 tc_status tc_analyze(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, int64_t* tv_dev, double* cc_dev,
@@ -468,11 +475,12 @@ tc_status tc_analyze(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, int64_
   *count_out = total;
   if (total > cap) return fail(ctx, TC_ERR_CAPACITY, "listing needs %lld triples, capacity %lld",
                                static_cast<long long>(total), static_cast<long long>(cap));
-  // pass 2: write the triples
+  // pass 2: write the triples (the hub schedule of pass 1 is still in the workspace)
   a.total = nullptr;
   a.tv = nullptr;
   a.tri = tri_dev;
   a.cap = cap;
+  a.reuse_hub = true;
   return finish(ctx, s, tc::launch_count(ctx, tc::MODE_LIST_WRITE, a, w, s));
 }
 

@@ -315,7 +315,7 @@ __device__ __forceinline__ uint32_t tile_batch(TileSmem& sm, int top, int32_t u,
   bool is_short;
   int32_t len;
   batch_setup(bs, a, ws, u, act, eg, vl, lo, vlen, tot, is_short, len, err, MODE == MODE_LIST_WRITE, 0u,
-              vbase + vl, vlen, a.hub_min > 0 ? 2 : 0);
+              vbase + vl, vlen, a.hub_min > 0 ? (a.reuse_hub ? 1 : 2) : 0);
   int qn = 0;
   for (int32_t p0 = 0; p0 < tot; p0 += 32 * kTileUnroll) {
     int32_t w[kTileUnroll];
@@ -667,7 +667,7 @@ __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab
   // listing a vertex hashed in several chunks: an edge's triples continue where the last chunk stopped
   const uint32_t erun0 = (MODE == MODE_LIST_WRITE && chunked && !first_chunk && act) ? ws.erun[eg] : 0u;
   // block kernel: edges bound for the hub side are recorded once, with the first chunk
-  const int hub_mode = (HUB || a.hub_min <= 0) ? 0 : (first_chunk ? 2 : 1);
+  const int hub_mode = (HUB || a.hub_min <= 0) ? 0 : ((first_chunk && !a.reuse_hub) ? 2 : 1);
   int32_t excl = 0;
   batch_setup(bs, a, ws, u, act, eg, 0, 0, 0, tot, is_short, len, err, MODE == MODE_LIST_WRITE, erun0, v, dv,
               hub_mode, &excl);
@@ -987,7 +987,7 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
       k_off32<<<n_grid, 256, 0, s>>>(a.n, a.m, a.offsets, const_cast<int32_t*>(a.off32));
       counted(ctx);
     }
-    if (hub) {
+    if (hub && !a.reuse_hub) {
       k_hub_list<<<n_grid, 256, 0, s>>>(a.n, a.offsets, a.hub_min, ws);
       counted(ctx);
     }
@@ -1017,7 +1017,7 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
   }
   counted(ctx, 2);
   if (hub) {
-    {
+    if (!a.reuse_hub) {
       Stage st(ctx, s, kNames[MODE][2]);
       // hub_off = scan of the per-hub counts (as many as there are hubs, read on the device)
       e = exclusive_scan_i32(ws.hub_cnt, ws.hub_off, a.n, ws.hub_scan, s, ws.counters + kCtrHubs);
@@ -1075,7 +1075,8 @@ int persistent_blocks(Ctx* ctx, const void* kernel, int threads, size_t dyn_smem
 }
 
 cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a_in, CountWs ws, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(ws.counters, 0, sizeof(uint32_t) * kCtrSlots, s);
+  // a write pass reusing the hub schedule keeps the hub and item counts of the counting pass
+  cudaError_t e = cudaMemsetAsync(ws.counters, 0, sizeof(uint32_t) * (a_in.reuse_hub ? kCtrHubs : kCtrSlots), s);
   if (e != cudaSuccess) return e;
   if (a_in.n <= 0) return cudaGetLastError();
   CountArgs a = a_in;

@@ -209,6 +209,8 @@ struct CountArgs {
   int32_t tile_quota = 0;                     // chunks per warp before its block retires (0: until the work ends)
   const int32_t* off32 = nullptr;             // int32 copy of offsets (set by launch_count when m < 2^31)
   int32_t v_lo = 0, v_hi = -1;                // apex vertices counted: [v_lo, v_hi) (-1: n)
+  bool reuse_hub = false;                     // listing write pass: the hub schedule of the counting pass that
+                                              // ran just before on the same workspace and thresholds is still valid
 };
 cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a, CountWs ws, cudaStream_t s);
 // Listing: eoff = exclusive scan of ecount (after a MODE_LIST_COUNT or MODE_LOCAL pass).

@@ -228,6 +228,7 @@ cudaError_t launch_request(tc_server* s, Request& r, GraphRec& g) {
         e = cudaMemcpyAsync(sl.h_total, w.eoff + g.m, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
     } else {
       tc::CountArgs a{g.n, g.m, g.offsets, g.cols, nullptr, nullptr, r.tri, static_cast<int64_t>(r.T)};
+      a.reuse_hub = true;  // phase 0 built the hub schedule in this workspace with the same slot settings
       if (e == cudaSuccess) e = tc::launch_count(ctx, tc::MODE_LIST_WRITE, a, w, st);
     }
   }
