@@ -619,9 +619,10 @@ def main():
     tuned = None
     if not args.no_tune:  # pick the cost-bin threshold on this graph (outside the timed region)
         from paper_1706_05151_gb300 import autotune
-        best, times, hub, hub_times = autotune.tune(g, ctx, record=False)
-        tuned = {"tile_max": best, "count_ms_by_tile_max": {str(k): round(v, 3) for k, v in times.items()},
-                 "hub_min": hub, "count_ms_by_hub_min": {str(k): round(v, 3) for k, v in hub_times.items()}}
+        # tuned on the per-vertex pass: with the listing write pass it is most of the step
+        best, times, hub, hub_times = autotune.tune(g, ctx, record=False, local=True)
+        tuned = {"tile_max": best, "local_ms_by_tile_max": {str(k): round(v, 3) for k, v in times.items()},
+                 "hub_min": hub, "local_ms_by_hub_min": {str(k): round(v, 3) for k, v in hub_times.items()}}
         g, T, tv, cc, tri, sp = step()
     W = int((g.deg.to(torch.int64) * g.dhat.to(torch.int64)).sum().item())
     assert int(tv.sum().item()) == 3 * T and len(tri) == T

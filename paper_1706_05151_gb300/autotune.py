@@ -49,33 +49,42 @@ def save_table(table: dict, path: str = TABLE_PATH):
     os.replace(tmp, path)
 
 
-def time_count(tc, g, ctx, tile_max: int, repeats: int, hub_min: int = 0) -> float:
+def time_count(tc, g, ctx, tile_max: int, repeats: int, hub_min: int = 0, local: bool = False) -> float:
+    """ms of one tc_count (or, with local, one per-vertex tc_count_local) at these thresholds."""
     ctx.set_tuning(tile_max, 1)
     ctx.set_hub_min(hub_min)
-    out = torch.empty(1, dtype=torch.int64, device=ctx.device)
-    tc.count(g, ctx, out=out)  # warm-up
+    if local:
+        def run():
+            tc.count_local(g, clustering=False, ctx=ctx)
+    else:
+        out = torch.empty(1, dtype=torch.int64, device=ctx.device)
+
+        def run():
+            tc.count(g, ctx, out=out)
+    run()  # warm-up
     stream = torch.cuda.current_stream(ctx.device)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(repeats):
-        tc.count(g, ctx, out=out)
+        run()
     e1.record(stream)
     torch.cuda.synchronize(ctx.device)
     return e0.elapsed_time(e1) / repeats
 
 
 def tune(g, ctx=None, candidates=CANDIDATES, repeats: int = 3, record: bool = True, path: str = TABLE_PATH,
-         hub_candidates=HUB_CANDIDATES):
+         hub_candidates=HUB_CANDIDATES, local: bool = False):
     """Time every candidate tile_max on g, then every hub_min at the best
-    tile_max; apply and (optionally) record the best pair.
+    tile_max; apply and (optionally) record the best pair.  local: time the
+    per-vertex pass (tc_count_local) instead of the plain count.
 
     Returns (best tile_max, {candidate: ms}, best hub_min, {candidate: ms}).
     """
     import paper_1706_05151_gb300 as tc
     ctx = ctx or tc.default_context()
-    times = {t: time_count(tc, g, ctx, t, repeats) for t in candidates}
+    times = {t: time_count(tc, g, ctx, t, repeats, local=local) for t in candidates}
     best = min(times, key=times.get)
-    hub_times = {h: time_count(tc, g, ctx, best, repeats, h) for h in hub_candidates}
+    hub_times = {h: time_count(tc, g, ctx, best, repeats, h, local=local) for h in hub_candidates}
     best_hub = min(hub_times, key=hub_times.get)
     ctx.set_tuning(best, 1)
     ctx.set_hub_min(best_hub)
