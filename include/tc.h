@@ -164,9 +164,9 @@ tc_status tc_workspace_size(tc_op op, int32_t n, int64_t m, size_t* bytes);
  * The order is u precedes v iff d_u < d_v, or d_u = d_v and u < v (Eq. (1));
  * each N_v is sorted ascending by id (Figure 2).  Ids outside [0, n),
  * self-loops and repeated edges give TC_ERR_INVALID_GRAPH (outputs are then
- * unspecified but every access stays in bounds).  Lists longer than 32768
- * give TC_ERR_UNSUPPORTED (the order bounds |N_v| by sqrt(2m), so this needs
- * m above about 5.4e8 and an adversarial graph).
+ * unspecified but every access stays in bounds).  Lists longer than 2^24 ids
+ * give TC_ERR_UNSUPPORTED (the degree order bounds |N_v| by sqrt(2m); lists
+ * beyond 32768 ids, possible under other orders, are sorted in global memory).
  */
 tc_status tc_orient(tc_ctx* ctx, int32_t n, int64_t m, const int32_t* edges, int64_t* offsets,
                     int32_t* cols, int32_t* deg, int32_t* dhat, void* ws, size_t ws_bytes,
