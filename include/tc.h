@@ -252,9 +252,10 @@ tc_status tc_analyze(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, int64_
  * Keep each undirected edge {a, b} independently with probability q and
  * count the triangles T' of the kept graph, whose orientation is the one of
  * the ORIGINAL degrees (the order is fixed before sampling).  The coin of
- * {a, b} is Philox4x64-10 (Salmon et al., SC'11) with counter
- * (min(a,b), max(a,b), 0, 0) and key (seed, 0): keep iff (w0 >> 11) < ceil(q * 2^53),
- * i.e. (w0 >> 11) * 2^-53 < q, where w0 is the first output word.
+ * {a, b} is Philox4x32-10 (Salmon et al., SC'11) with 32-bit counter words
+ * (min(a,b), max(a,b), 0, 0) and key (lo32(seed), hi32(seed)): with r the top 53
+ * bits of the first two output words (r = x0 * 2^21 + (x1 >> 11)), keep iff
+ * r < ceil(q * 2^53), i.e. r * 2^-53 < q.
  *   q in [0, 1]; kept_tri_dev device uint64[1] (T'); kept_edges_dev device
  *   int64[1] (edges kept).  The unbiased estimate of T is T' / q^3 (Section 9.1),
  *   computed by the caller on the host.
@@ -268,8 +269,8 @@ tc_status tc_sparsify_count(tc_ctx* ctx, const tc_graph* g, double q, uint64_t s
  * sparsifies the partition it loads, Figure "sparsification"): the triangles
  * whose apex (first vertex in the order of Eq. (1)) lies in [v_begin, v_end),
  * counted on the graph in which this part keeps each edge with probability q
- * by its own coin -- Philox4x64-10 with counter (min(a,b), max(a,b), part, 0)
- * and key (seed, 0), keep iff (w0 >> 11) < ceil(q * 2^53).  part = 0 draws the
+ * by its own coin -- Philox4x32-10 with counter words (min(a,b), max(a,b), part, 0)
+ * and the key above, keep iff r < ceil(q * 2^53).  part = 0 draws the
  * coins of tc_sparsify_count.  Run over the parts of a partition, each with its
  * own index, sum T'/q^3 is unbiased, and two triangles of different parts that
  * share an edge survive independently, so the variance is Eq. var2's (k' <= k).

@@ -28,6 +28,7 @@ _lib = None
 i32p = ctypes.POINTER(ctypes.c_int32)
 i64p = ctypes.POINTER(ctypes.c_int64)
 u64p = ctypes.POINTER(ctypes.c_uint64)
+u32p = ctypes.POINTER(ctypes.c_uint32)
 f64p = ctypes.POINTER(ctypes.c_double)
 
 ERRORS = {1: "vertex id out of range", 2: "self-loop", 3: "repeated edge", 4: "out of memory",
@@ -71,12 +72,12 @@ def _load():
         lib.orc_vertex_triangles.restype = ctypes.c_int64
         lib.orc_vertex_triangles.argtypes = [i64p, i32p, ctypes.c_int32]
         lib.orc_philox.restype = None
-        lib.orc_philox.argtypes = [u64p, u64p, u64p]
+        lib.orc_philox.argtypes = [u32p, u32p, u32p]
         lib.orc_sparsify_keep.restype = ctypes.c_int
         lib.orc_sparsify_keep.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double]
         lib.orc_sparsify_keep_part.restype = ctypes.c_int
         lib.orc_sparsify_keep_part.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double,
-                                               ctypes.c_uint64]
+                                               ctypes.c_uint32]
         lib.orc_sparsify_count.restype = ctypes.c_int
         lib.orc_sparsify_count.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, ctypes.c_uint64,
                                            ctypes.c_double, u64p, i64p, f64p]
@@ -190,10 +191,12 @@ def clustering(deg: np.ndarray, tv: np.ndarray) -> np.ndarray:
 
 
 def philox(ctr, key) -> np.ndarray:
-    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint64))
-    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint64))
-    out = np.zeros(4, dtype=np.uint64)
-    _load().orc_philox(_p(c, u64p), _p(k, u64p), _p(out, u64p))
+    """Philox4x32-10 (Salmon et al., SC'11): four 32-bit counter words and two
+    32-bit key words in, four 32-bit words out."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    _load().orc_philox(_p(c, u32p), _p(k, u32p), _p(out, u32p))
     return out
 
 
@@ -280,8 +283,9 @@ def count_apex_range(n: int, edges, lo: int, hi: int):
 # ---- sparsification with partition-local coins (Section 9.2) ----
 
 def sparsify_keep_part(a: int, b: int, seed: int, q: float, part: int) -> bool:
-    """The coin of edge {a, b} drawn by part `part`: Philox4x64-10 with counter
-    (min, max, part, 0) and key (seed, 0); kept iff (w0 >> 11) * 2^-53 < q."""
+    """The coin of edge {a, b} drawn by part `part`: Philox4x32-10 with counter
+    (min, max, part, 0) and key (lo32(seed), hi32(seed)); with r the top 53 bits
+    of the output words x0:x1, kept iff r * 2^-53 < q."""
     return bool(_load().orc_sparsify_keep_part(int(a), int(b), int(seed), float(q), int(part)))
 
 

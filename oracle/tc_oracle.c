@@ -34,10 +34,11 @@
  *   - the order's degree is the undirected degree of the simple graph;
  *   - ties of the order are broken by the smaller id first;
  *   - C_v = 0 when d_v < 2;
- *   - sparsification's coin for the undirected edge {a, b} is Philox4x64-10
- *     (Salmon et al., SC'11) with counter (min(a,b), max(a,b), 0, 0) and key
- *     (seed, 0); the edge is kept iff the first output word w satisfies
- *     (w >> 11) * 2^-53 < q;
+ *   - sparsification's coin for the undirected edge {a, b} is Philox4x32-10
+ *     (Salmon et al., SC'11) with 32-bit counter words (min(a,b), max(a,b),
+ *     0, 0) and key (low, high 32 bits of the seed); with x0, x1 the first two
+ *     output words, r = x0 * 2^21 + (x1 >> 11) is the top 53 bits of the
+ *     64-bit word x0:x1, and the edge is kept iff r * 2^-53 < q;
  *   - the sparsified graph keeps the order of the ORIGINAL degrees (Figure
  *     "sparsification" compares with the order fixed while loading).
  */
@@ -244,21 +245,22 @@ int64_t orc_vertex_triangles(const int64_t* adj_off, const int32_t* adj, int32_t
   return t;
 }
 
-/* ---- Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) ------------------ */
-static void orc_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4]) {
-  const uint64_t mul0 = 0xD2E7470EE14C6C93ULL, mul1 = 0xCA5A826395121157ULL;
-  const uint64_t weyl0 = 0x9E3779B97F4A7C15ULL, weyl1 = 0xBB67AE8584CAA73BULL;
-  uint64_t x0 = ctr_in[0], x1 = ctr_in[1], x2 = ctr_in[2], x3 = ctr_in[3];
-  uint64_t k0 = key_in[0], k1 = key_in[1];
+/* ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ------------------
+ * Ten rounds; each multiplies words 0 and 2 by the round multipliers into
+ * 64-bit products, xors the high halves with words 1 and 3 and the round key,
+ * permutes the words, and bumps the key by the Weyl constants. */
+static void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  const uint32_t mul0 = 0xD2511F53u, mul1 = 0xCD9E8D57u;
+  const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;
+  uint32_t x0 = ctr_in[0], x1 = ctr_in[1], x2 = ctr_in[2], x3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
   for (int round = 0; round < 10; ++round) {
-    unsigned __int128 p = (unsigned __int128)mul0 * x0;
-    unsigned __int128 r = (unsigned __int128)mul1 * x2;
-    uint64_t hi_p = (uint64_t)(p >> 64), lo_p = (uint64_t)p;
-    uint64_t hi_r = (uint64_t)(r >> 64), lo_r = (uint64_t)r;
-    uint64_t y0 = hi_r ^ x1 ^ k0;
-    uint64_t y1 = lo_r;
-    uint64_t y2 = hi_p ^ x3 ^ k1;
-    uint64_t y3 = lo_p;
+    uint64_t p = (uint64_t)mul0 * x0;
+    uint64_t r = (uint64_t)mul1 * x2;
+    uint32_t y0 = (uint32_t)(r >> 32) ^ x1 ^ k0;
+    uint32_t y1 = (uint32_t)r;
+    uint32_t y2 = (uint32_t)(p >> 32) ^ x3 ^ k1;
+    uint32_t y3 = (uint32_t)p;
     x0 = y0; x1 = y1; x2 = y2; x3 = y3;
     k0 += weyl0;
     k1 += weyl1;
@@ -266,12 +268,12 @@ static void orc_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2]
   out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* Exposed so a test can compare it against a library Philox4x64-10. */
-void orc_philox(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
-  orc_philox4x64_10(ctr, key, out);
+/* Exposed so a test can compare it against the published known answers. */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  orc_philox4x32_10(ctr, key, out);
 }
 
-int orc_sparsify_keep_part(int32_t a, int32_t b, uint64_t seed, double q, uint64_t part);
+int orc_sparsify_keep_part(int32_t a, int32_t b, uint64_t seed, double q, uint32_t part);
 
 /*
  * The sparsification coin of Section 9.1: edge {a, b} is retained with
@@ -287,12 +289,13 @@ int orc_sparsify_keep(int32_t a, int32_t b, uint64_t seed, double q) {
  * partition it loads (Section 9.2): the same generator with the part's index
  * as the third counter word; part 0 is the coin above.
  */
-int orc_sparsify_keep_part(int32_t a, int32_t b, uint64_t seed, double q, uint64_t part) {
-  uint64_t ctr[4] = {(uint64_t)(a < b ? a : b), (uint64_t)(a < b ? b : a), part, 0};
-  uint64_t key[2] = {seed, 0};
-  uint64_t out[4];
-  orc_philox4x64_10(ctr, key, out);
-  double u = (double)(out[0] >> 11) * 0x1.0p-53;
+int orc_sparsify_keep_part(int32_t a, int32_t b, uint64_t seed, double q, uint32_t part) {
+  uint32_t ctr[4] = {(uint32_t)(a < b ? a : b), (uint32_t)(a < b ? b : a), part, 0};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t out[4];
+  orc_philox4x32_10(ctr, key, out);
+  uint64_t r = ((uint64_t)out[0] << 21) | (out[1] >> 11); /* top 53 bits of x0:x1 */
+  double u = (double)r * 0x1.0p-53;
   return u < q;
 }
 

@@ -530,7 +530,7 @@ tc_status tc_sparsify_count_part(tc_ctx* ctx, const tc_graph* g, double q, uint6
   Carver c(ws);
   tc::SparsifyWs w = tc::carve_sparsify(c, g->n, g->m);
   const uint64_t t53 = static_cast<uint64_t>(std::ceil(q * 9007199254740992.0));
-  cudaError_t e = tc::launch_sparsify(ctx, g->n, g->m, g->offsets, g->cols, t53, seed, static_cast<uint64_t>(part), w,
+  cudaError_t e = tc::launch_sparsify(ctx, g->n, g->m, g->offsets, g->cols, t53, seed, static_cast<uint32_t>(part), w,
                                       kept_edges_dev, s);
   if (e == cudaSuccess && v_end > v_begin) {
     tc::CountArgs a{g->n, g->m, w.offsets, w.cols, reinterpret_cast<unsigned long long*>(kept_tri_dev), nullptr,

@@ -218,7 +218,7 @@ cudaError_t launch_list_offsets(Ctx* ctx, int64_t m, CountWs ws, cudaStream_t s)
 cudaError_t launch_clustering(Ctx* ctx, int32_t n, const int32_t* deg, const int64_t* tv, double* cc, cudaStream_t s);
 
 cudaError_t launch_sparsify(Ctx* ctx, int32_t n, int64_t m, const int64_t* offsets, const int32_t* cols,
-                            uint64_t threshold53, uint64_t seed, uint64_t part, SparsifyWs ws, int64_t* kept_edges,
+                            uint64_t threshold53, uint64_t seed, uint32_t part, SparsifyWs ws, int64_t* kept_edges,
                             cudaStream_t s);
 
 // Grid of a persistent kernel: resident blocks per SM times the SM count.

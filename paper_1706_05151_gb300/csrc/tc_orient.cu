@@ -13,7 +13,8 @@
 //   k_scatter       third pass: cols[offsets[src] + cursor[src]++] = dst
 //   k_sort_small    one thread per vertex: lists of <= 32 ids sorted in
 //                   registers by a bitonic network sized to the warp's longest
-//                   list; longer lists are queued
+//                   list, the warp's run of lists staged in shared memory;
+//                   longer lists are queued
 //   k_sort_big      one block per queued list: bitonic sort in shared memory
 // Sorted lists are checked for repeated ids (a repeated edge of the input).
 #include <algorithm>
@@ -190,19 +191,31 @@ __device__ __forceinline__ void sort_list_regs(int32_t* __restrict__ p, int len,
 }
 
 // One thread per vertex.  The network size is the warp's longest short list
-// rounded up to a power of two, so one warp runs one network.
-__global__ void k_sort_small(int32_t n, const int64_t* __restrict__ offsets, int32_t* __restrict__ cols,
-                             int32_t* __restrict__ big_queue, int32_t* __restrict__ mid_queue,
-                             uint32_t* __restrict__ counters, uint32_t* err) {
+// rounded up to a power of two, so one warp runs one network.  The 32 lists of
+// a warp are one contiguous run of cols; when the run fits kSortStage ids the
+// warp copies it to shared memory and back with coalesced accesses, so that
+// the threads' element-wise loads and stores of their own lists stay on chip
+// (otherwise each of those global stores is 32 scattered sector writes).
+constexpr int kSortSmallThreads = 256;
+constexpr int kSortStage = 1024;  // ids per warp staged in shared memory
+__global__ void __launch_bounds__(kSortSmallThreads) k_sort_small(int32_t n, const int64_t* __restrict__ offsets,
+                                                                  int32_t* __restrict__ cols,
+                                                                  int32_t* __restrict__ big_queue,
+                                                                  int32_t* __restrict__ mid_queue,
+                                                                  uint32_t* __restrict__ counters, uint32_t* err) {
+  __shared__ int32_t s_run[kSortSmallThreads / 32][kSortStage];
+  int32_t* run = s_run[threadIdx.x >> 5];
+  const int lane = lane_id();
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   // whole warps iterate together so the warp-wide reduction below is legal
   for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < n; base += stride) {
     const int64_t v = base + threadIdx.x;
     int len = 0;
-    int64_t beg = 0;
+    int64_t beg = 0, end = 0;
     if (v < n) {
       beg = offsets[v];
-      const int64_t l = offsets[v + 1] - beg;
+      end = offsets[v + 1];
+      const int64_t l = end - beg;
       if (l > kSortWarpCap) {
         big_queue[atomicAdd(&counters[0], 1u)] = static_cast<int32_t>(v);
       } else if (l > 32) {
@@ -212,13 +225,30 @@ __global__ void k_sort_small(int32_t n, const int64_t* __restrict__ offsets, int
       }
     }
     const int wmax = __reduce_max_sync(FULL, len);
-    int32_t* p = cols + beg;
     if (wmax <= 1) continue;
+    // the warp's run [first, last): lanes past n hold no list
+    const int nv = static_cast<int>(min64(32, n - (v - lane)));
+    const int64_t first = __shfl_sync(FULL, beg, 0);
+    const int64_t last = __shfl_sync(FULL, end, nv - 1);
+    const bool staged = last - first <= kSortStage && first >= 0 && last >= first;
+    int32_t* p = cols + beg;
+    if (staged) {
+      const int span = static_cast<int>(last - first);
+      for (int i = lane; i < span; i += 32) run[i] = cols[first + i];
+      __syncwarp();
+      p = run + (beg - first);
+    }
     if (wmax <= 2) sort_list_regs<2>(p, len, err);
     else if (wmax <= 4) sort_list_regs<4>(p, len, err);
     else if (wmax <= 8) sort_list_regs<8>(p, len, err);
     else if (wmax <= 16) sort_list_regs<16>(p, len, err);
     else sort_list_regs<32>(p, len, err);
+    if (staged) {
+      __syncwarp();
+      const int span = static_cast<int>(last - first);
+      for (int i = lane; i < span; i += 32) cols[first + i] = run[i];
+      __syncwarp();
+    }
   }
 }
 
@@ -379,10 +409,11 @@ cudaError_t launch_orient(Ctx* ctx, int32_t n, int64_t m, const int32_t* edges, 
     counted(ctx);
   }
   if (n > 0) {
-    const int grid_v = static_cast<int>(min64((n + 255) / 256, static_cast<int64_t>(ctx->sm_count) * 16));
+    const int grid_v = static_cast<int>(
+        min64((n + kSortSmallThreads - 1) / kSortSmallThreads, static_cast<int64_t>(ctx->sm_count) * 16));
     {
       Stage st(ctx, s, "orient.sort_small");
-      k_sort_small<<<grid_v, 256, 0, s>>>(n, offsets, cols, ws.big_queue, ws.mid_queue, ws.counters, ctx->d_err);
+      k_sort_small<<<grid_v, kSortSmallThreads, 0, s>>>(n, offsets, cols, ws.big_queue, ws.mid_queue, ws.counters, ctx->d_err);
     }
     {
       Stage st(ctx, s, "orient.sort_mid");

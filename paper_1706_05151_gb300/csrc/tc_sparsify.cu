@@ -4,18 +4,22 @@
 // triangle count T' gives the unbiased estimate T'/q^3.
 //
 // The coin of undirected edge {a, b} depends only on the edge:
-// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) with counter
-// (min(a,b), max(a,b), 0, 0) and key (seed, 0); keep iff (w0 >> 11) < t53,
-// where t53 = ceil(q * 2^53) is computed on the host.  With partition-local
-// coins (Section 9.2, tc_sparsify_count_part) the third counter word is the
-// part's index, so each part draws its own coin for every edge it holds.
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with 32-bit counter words
+// (min(a,b), max(a,b), 0, 0) and key (lo32(seed), hi32(seed)); with r the top
+// 53 bits of the output words x0:x1, keep iff r < t53, where
+// t53 = ceil(q * 2^53) is computed on the host.  With partition-local coins
+// (Section 9.2, tc_sparsify_count_part) the third counter word is the part's
+// index, so each part draws its own coin for every edge it holds.  The 32-bit
+// variant keeps the coin to two 32x32->64 products per round; the 64-bit one
+// spends about four times the integer issue slots on emulated 64-bit products.
 //
 // GB300 mapping: a warp takes 32 consecutive vertices, whose lists are one
 // contiguous run of cols; lanes walk that run 32 ids at a time (coalesced), and
 // find their source vertex by a 5-step search over the 32 list starts.
 //   k_mark     coin per oriented edge -> keep[] bytes and kept count per vertex
 //   scan       kept counts -> kept CSR offsets
-//   k_compact  copy the kept ids, order preserved, into the kept CSR
+//   k_compact  copy the kept ids, order preserved, into the kept CSR (a
+//              stream compaction over runs of 64 vertices' lists)
 #include <algorithm>
 
 #include "tc_internal.cuh"
@@ -35,23 +39,27 @@ SparsifyWs carve_sparsify(Carver& c, int32_t n, int64_t m) {
 
 namespace {
 
-__device__ __forceinline__ uint64_t philox4x64_10_w0(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
-                                                     uint64_t k0, uint64_t k1) {
-  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
-  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+// Top 53 bits of words 0 and 1 of Philox4x32-10 (ten rounds of two 32x32->64
+// products, xor of the high halves with the other words and the round key,
+// then a Weyl step of the key).
+__device__ __forceinline__ uint64_t philox4x32_10_top53(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                        uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint64_t lo0 = M0 * c0, hi0 = __umul64hi(M0, c0);
-    const uint64_t lo1 = M1 * c2, hi1 = __umul64hi(M1, c2);
-    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    const uint64_t p0 = static_cast<uint64_t>(M0) * c0;
+    const uint64_t p1 = static_cast<uint64_t>(M1) * c2;
+    const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c1 ^ k0;
+    const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c3 ^ k1;
     c0 = n0;
-    c1 = lo1;
+    c1 = static_cast<uint32_t>(p1);
     c2 = n2;
-    c3 = lo0;
+    c3 = static_cast<uint32_t>(p0);
     k0 += W0;
     k1 += W1;
   }
-  return c0;
+  return (static_cast<uint64_t>(c0) << 21) | (c1 >> 11);
 }
 
 // Per-warp view of 32 consecutive vertices [vb, vb+32) and their id run.
@@ -93,10 +101,12 @@ __device__ __forceinline__ int owner(const int64_t* s_beg, int64_t idx) {
 }
 
 constexpr int kSpWarps = 8;
+constexpr int kSpUnroll = 4;  // windows of 32 ids whose loads one warp keeps in flight
+constexpr int kCompactSpan = 64;  // vertices per warp task, k_compact
 
 __global__ void __launch_bounds__(kSpWarps * 32) k_mark(int32_t n, int64_t m, const int64_t* __restrict__ off,
                                                         const int32_t* __restrict__ cols, uint64_t t53,
-                                                        uint64_t seed, uint64_t part, uint8_t* __restrict__ keep,
+                                                        uint64_t seed, uint32_t part, uint8_t* __restrict__ keep,
                                                         int32_t* __restrict__ kept_count, uint32_t* err) {
   __shared__ int64_t s_beg[kSpWarps][32];
   __shared__ int32_t s_cnt[kSpWarps][32];
@@ -109,58 +119,78 @@ __global__ void __launch_bounds__(kSpWarps * 32) k_mark(int32_t n, int64_t m, co
     if (!ok) continue;
     s_cnt[wid][lane] = 0;
     __syncwarp();
-    for (int64_t idx = r.first + lane; idx < r.last; idx += 32) {
-      const int s = owner(s_beg[wid], idx);
-      const uint64_t v = static_cast<uint64_t>(vb + s);
-      const uint64_t u = static_cast<uint64_t>(static_cast<uint32_t>(cols[idx]));
-      const uint64_t w0 = philox4x64_10_w0(v < u ? v : u, v < u ? u : v, part, 0, seed, 0);
-      const bool k = (w0 >> 11) < t53;
-      keep[idx] = k ? 1 : 0;
-      if (k) atomicAdd(&s_cnt[wid][s], 1);
+    // kSpUnroll windows of 32 ids per round: their loads are issued together
+    for (int64_t base = r.first; base < r.last; base += 32 * kSpUnroll) {
+      uint32_t u[kSpUnroll];
+#pragma unroll
+      for (int j = 0; j < kSpUnroll; ++j) {
+        const int64_t idx = base + 32 * j + lane;
+        u[j] = idx < r.last ? static_cast<uint32_t>(cols[idx]) : 0u;
+      }
+#pragma unroll
+      for (int j = 0; j < kSpUnroll; ++j) {
+        const int64_t idx = base + 32 * j + lane;
+        if (idx < r.last) {
+          const int s = owner(s_beg[wid], idx);
+          const uint32_t v = static_cast<uint32_t>(vb + s);
+          const uint64_t r53 = philox4x32_10_top53(v < u[j] ? v : u[j], v < u[j] ? u[j] : v, part, 0,
+                                                   static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+          const bool k = r53 < t53;
+          keep[idx] = k ? 1 : 0;
+          if (k) atomicAdd(&s_cnt[wid][s], 1);
+        }
+      }
     }
     __syncwarp();
     if (vb + lane < n) kept_count[vb + lane] = s_cnt[wid][lane];
   }
 }
 
+// The kept ids of consecutive vertices are contiguous in the kept CSR, in the
+// order of cols, so placing them is a stream compaction: the kept ids of
+// vertices [vb, ve) go to new_cols[new_off[vb] ...] in order.  A warp takes
+// kCompactSpan vertices at a time and advances one running count by the
+// ballot of each window; no per-list bookkeeping is needed.
 __global__ void __launch_bounds__(kSpWarps * 32) k_compact(int32_t n, int64_t m, const int64_t* __restrict__ off,
                                                            const int32_t* __restrict__ cols,
                                                            const uint8_t* __restrict__ keep,
                                                            const int64_t* __restrict__ new_off,
                                                            int32_t* __restrict__ new_cols, uint32_t* err) {
-  __shared__ int64_t s_beg[kSpWarps][32];
-  __shared__ int64_t s_run[kSpWarps][32];
-  const int lane = lane_id(), wid = threadIdx.x >> 5;
+  const int lane = lane_id();
   const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t vb = gw * 32; vb < n; vb += nwarps * 32) {
-    bool ok;
-    const Run r = load_run(static_cast<int32_t>(vb), n, m, off, s_beg[wid], err, ok);
-    if (!ok) continue;
-    s_run[wid][lane] = (vb + lane < n) ? new_off[vb + lane] : 0;
-    __syncwarp();
-    for (int64_t w0 = r.first; w0 < r.last; w0 += 32) {
-      const int64_t idx = w0 + lane;
-      const bool act = idx < r.last;
-      const int s = act ? owner(s_beg[wid], idx) : 31;
-      const bool k = act && keep[idx];
-      const unsigned mask = __ballot_sync(FULL, k);
-      // lanes of the same list are contiguous in the window; count kept ones before me
-      const int64_t seg_start = s_beg[wid][s];
-      const int first_lane = static_cast<int>(max64(seg_start - w0, 0));
-      const unsigned before = mask & ((1u << lane) - 1u) & ~((1u << first_lane) - 1u);
-      const int64_t dst = s_run[wid][s] + __popc(before);
-      if (k) new_cols[dst] = cols[idx];
-      // the last lane of each list in this window advances that list's cursor
-      const int s_next = __shfl_down_sync(FULL, s, 1);
-      const bool last_of_seg = act && (lane == 31 || s_next != s || idx + 1 >= r.last);
-      __syncwarp();
-      if (last_of_seg) {
-        const unsigned upto = (lane == 31) ? FULL : ((1u << (lane + 1)) - 1u);
-        s_run[wid][s] += __popc(mask & upto & ~((1u << first_lane) - 1u));
-      }
-      __syncwarp();
+  for (int64_t vb = gw * kCompactSpan; vb < n; vb += nwarps * kCompactSpan) {
+    const int64_t ve = min64(n, vb + kCompactSpan);
+    const int64_t first = off[vb], last = off[ve];
+    const int64_t base = new_off[vb], base_end = new_off[ve];
+    if (first < 0 || last < first || last > m || base < 0 || base_end < base || base_end - base > last - first) {
+      if (lane == 0) set_err(err, ERR_BAD_CSR);
+      continue;
     }
+    const int64_t room = base_end - base;
+    int64_t done = 0;  // kept ids of this span placed so far
+    for (int64_t p0 = first; p0 < last; p0 += 32 * kSpUnroll) {
+      bool kk[kSpUnroll];
+      int32_t c[kSpUnroll];
+#pragma unroll
+      for (int j = 0; j < kSpUnroll; ++j) {
+        const int64_t idx = p0 + 32 * j + lane;
+        const bool act = idx < last;
+        kk[j] = act && keep[idx];
+        c[j] = act ? cols[idx] : 0;
+      }
+#pragma unroll
+      for (int j = 0; j < kSpUnroll; ++j) {
+        const unsigned mask = __ballot_sync(FULL, kk[j]);
+        const int64_t r = done + __popc(mask & ((1u << lane) - 1u));
+        if (kk[j]) {
+          if (r < room) new_cols[base + r] = c[j];
+          else set_err(err, ERR_BAD_CSR);  // keep bytes disagree with the kept counts
+        }
+        done += __popc(mask);
+      }
+    }
+    if (lane == 0 && done != room) set_err(err, ERR_BAD_CSR);
   }
 }
 
@@ -171,7 +201,7 @@ __global__ void k_copy_last(const int64_t* __restrict__ new_off, int32_t n, int6
 }  // namespace
 
 cudaError_t launch_sparsify(Ctx* ctx, int32_t n, int64_t m, const int64_t* offsets, const int32_t* cols,
-                            uint64_t threshold53, uint64_t seed, uint64_t part, SparsifyWs ws, int64_t* kept_edges,
+                            uint64_t threshold53, uint64_t seed, uint32_t part, SparsifyWs ws, int64_t* kept_edges,
                             cudaStream_t s) {
   cudaError_t e;
   if (n > 0) {
