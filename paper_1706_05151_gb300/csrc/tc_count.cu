@@ -419,16 +419,18 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, 
       if (big) ws.big_queue[qb + __popc(bigmask & lanemask_lt())] = v;
     }
     // Groups: maximal runs of consecutive short lists whose ids fit one tile.
-    int g0 = 0;
+    // live: lanes whose list this kernel counts (a live list has <= tile_max <= kTile ids, so it opens a group)
+    const unsigned live = __ballot_sync(FULL, valid && !big && !skip);
+    int g0 = live ? __ffs(live) - 1 : 32;
     while (g0 < 32) {
       const int32_t len = (lane >= g0 && valid && !big && !skip) ? static_cast<int32_t>(d) : 0;
       const int32_t incl = warp_incl_scan(len);
       const bool stop = lane >= g0 && (!valid || big || skip || incl > kTile);
       const unsigned smask = __ballot_sync(FULL, stop);
       const int g1 = smask ? __ffs(smask) - 1 : 32;
-      if (g1 == g0) {  // lane g0 is past the end, a queued long list or skipped
-        if (!__shfl_sync(FULL, valid, g0)) break;
-        ++g0;
+      if (g1 == g0) {  // lane g0 is past the end, a queued long list or skipped: go to the next live lane
+        const unsigned after = g0 < 31 ? live & (0xffffffffu << (g0 + 1)) : 0u;
+        g0 = after ? __ffs(after) - 1 : 32;
         continue;
       }
       const bool in_group = lane >= g0 && lane < g1;
@@ -465,7 +467,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, 
         const uint32_t c = tile_batch<MODE>(sm, top, u, act, start + t, vl, sm.vlo[vl], vlen,
                                             static_cast<int32_t>(base), a, ws, err);
         if (act && (MODE == MODE_LOCAL || MODE == MODE_LIST_COUNT) && ws.ecount)
-          ws.ecount[start + t] = static_cast<int32_t>(c);
+          __stcs(ws.ecount + start + t, static_cast<int32_t>(c));  // write-once stream: evict-first
         if (c) {
           if (MODE == MODE_LOCAL)
             atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + u), static_cast<unsigned long long>(c));

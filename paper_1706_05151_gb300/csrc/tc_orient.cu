@@ -7,7 +7,9 @@
 //
 // GB300 mapping (all HBM/L2 traffic, no tensor cores):
 //   k_degree        grid-stride over the edge list, 8-byte pair loads, RED.ADD
-//                   into deg[] (4n bytes, L2-resident for n <= 2^25)
+//                   into deg[] (4n bytes, L2-resident for n <= 2^25); the edge
+//                   stream is read evict-first in all three passes (and cols
+//                   written so) to keep deg[] in L2 for the random gathers
 //   k_orient_count  same pass shape, gathers deg[a], deg[b], counts dhat[src]
 //   exclusive scan  offsets = scan(dhat)
 //   k_scatter       third pass: cols[offsets[src] + cursor[src]++] = dst
@@ -87,7 +89,7 @@ __global__ void k_degree(const int2* __restrict__ edges, int64_t m, int32_t n, i
     int2 p = make_int2(0, 0);
     bool ok = false;
     if (e < m) {
-      p = edges[e];
+      p = __ldcs(edges + e);  // evict-first: the stream must not push deg[] out of L2
       ok = edge_ok(p, n, err);
     }
     int hl;
@@ -111,7 +113,7 @@ __global__ void k_orient_count(const int2* __restrict__ edges, int64_t m, int32_
     int32_t src = 0;
     bool ok = false;
     if (e < m) {
-      const int2 p = edges[e];
+      const int2 p = __ldcs(edges + e);
       ok = edge_valid(p, n);
       if (ok) src = precedes(order_key(deg, keys, p.x), p.x, order_key(deg, keys, p.y), p.y) ? p.x : p.y;
     }
@@ -131,7 +133,7 @@ __global__ void k_scatter(const int2* __restrict__ edges, int64_t m, int32_t n, 
     int32_t src = 0, dst = 0;
     bool ok = false;
     if (e < m) {
-      const int2 p = edges[e];
+      const int2 p = __ldcs(edges + e);
       ok = edge_valid(p, n);
       if (ok) {
         const bool fwd = precedes(order_key(deg, keys, p.x), p.x, order_key(deg, keys, p.y), p.y);
@@ -146,7 +148,7 @@ __global__ void k_scatter(const int2* __restrict__ edges, int64_t m, int32_t n, 
     base = __shfl_sync(FULL, base, hl);
     if (ok) {
       const int64_t pos = base + (lane - hl);
-      if (pos < offsets[src + 1]) cols[pos] = dst;
+      if (pos < offsets[src + 1]) __stcs(cols + pos, dst);
       else set_err(err, ERR_BAD_CSR);  // unreachable for a consistent count
     }
   }
