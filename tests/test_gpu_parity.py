@@ -206,6 +206,25 @@ def test_sparsify_q_one_is_exact(tc):
     assert mk == len(e) and t == tc.count(g)
 
 
+@pytest.mark.parametrize("make,n", [
+    (lambda: synth.er(1000, 6000, 31), 1000),              # n not a multiple of 32 or 64, isolated vertices
+    (lambda: synth.chung_lu(3001, 24.0, 2.1, 32), 3001),   # skewed degrees: long lists beside empty ones
+    (lambda: synth.complete(70), 70),                      # lists of 0 .. 69 ids, every edge in triangles
+    (lambda: synth.wheel(130), 131),                       # hub of degree 130 last in the order
+    (lambda: np.zeros((0, 2), np.int32), 65),              # no edges at all
+])
+@pytest.mark.parametrize("q", [0.05, 0.5])
+def test_sparsify_ragged_sizes(tc, make, n, q):
+    # the marking pass walks 32-vertex runs and the compaction 64-vertex runs:
+    # sizes that end mid-run, empty lists and long lists must all match the oracle
+    e = make()
+    g = tc.orient(to_dev(e), n)
+    for seed in (3, 4):
+        t, mk, _ = tc.sparsify_count(g, q, seed)
+        rt, rmk, _ = oracle.sparsify_count(n, e, seed, q)
+        assert (t, mk) == (rt, rmk)
+
+
 # ---- error handling -----------------------------------------------------------------
 
 def test_invalid_graphs_are_reported(tc):
