@@ -39,6 +39,8 @@
 // order -- fixed positions, no atomics, the same output every run.
 #include <algorithm>
 
+#include <type_traits>
+
 #include "tc_internal.cuh"
 
 namespace tc {
@@ -54,8 +56,8 @@ constexpr int kOwnCap = 32 * kShortLen;
 constexpr int kTileUnroll = 8;       // candidate windows in flight per lane, tile kernel
 constexpr int kBlockWarps = 8;       // warps per block, block kernel
 constexpr int kHashBatch = 32;       // walked lists a warp takes at a time (block and hub kernels, <= 32)
-constexpr int64_t kBegBias = 1024;   // beg >= -(32 * kShortLen): biased to stay non-negative when packed
-constexpr uint64_t kBegMask = (uint64_t(1) << 58) - 1;
+constexpr uint64_t kPtrMask = (uint64_t(1) << 58) - 1;  // packed list address: byte address below bit 58
+constexpr uint32_t kSaltMix = 0x7C000000u;              // filter salt (0..31) << 26: bits 58..62 of the packed word
 constexpr int kHubMinDefault = 64;   // default hub_min: lists of at least this many ids take their in-edges
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
@@ -119,36 +121,56 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x) {
   return x;
 }
 
-// Multiplicative hash of (salt, id) onto a 2^LOG2-bit filter.
+// Multiplicative hash of (salt, id) onto a 2^LOG2-bit filter; mix = salt << 26.
 template <int LOG2>
-__device__ __forceinline__ uint32_t fbit(int32_t w, int32_t salt) {
-  return ((static_cast<uint32_t>(w) ^ (static_cast<uint32_t>(salt) << 26)) * 0x9E3779B1u) >> (32 - LOG2);
+__device__ __forceinline__ uint32_t fbit(int32_t w, uint32_t mix) {
+  return ((static_cast<uint32_t>(w) ^ mix) * 0x9E3779B1u) >> (32 - LOG2);
 }
 
 template <int LOG2>
-__device__ __forceinline__ bool ftest(const uint32_t* bits, int32_t w, int32_t salt) {
-  const uint32_t h = fbit<LOG2>(w, salt);
-  return (bits[h >> 5] >> (h & 31)) & 1u;
+__device__ __forceinline__ bool ftest(const uint32_t* bits, int32_t w, uint32_t mix) {
+  const uint32_t h = fbit<LOG2>(w, mix);
+  // the funnel shift takes its amount modulo 32: bit (h & 31) of the word with no mask
+  return __funnelshift_r(bits[h >> 5], 0u, h) & 1u;
 }
 
 template <int LOG2>
-__device__ __forceinline__ void fset(uint32_t* bits, int32_t w, int32_t salt) {
-  const uint32_t h = fbit<LOG2>(w, salt);
+__device__ __forceinline__ void fset(uint32_t* bits, int32_t w, uint32_t mix) {
+  const uint32_t h = fbit<LOG2>(w, mix);
   atomicOr(&bits[h >> 5], 1u << (h & 31));
 }
 
 // Per-warp state of one batch of up to 32 oriented edges (v, u), one per lane.
-struct BatchSmem {
-  int64_t beg[32];        // short list: start of N_u minus its flattened offset; long list: start of N_u
-  uint64_t pk[32];        // tile kernel: beg + kBegBias in the low 58 bits, filter salt above (one load for both)
-  int32_t u[32];
-  int32_t lo[32];         // tile kernel: N_v's slice [lo, lo + len) of the tile
-  int32_t len[32];
-  int32_t salt[32];       // tile kernel: filter salt (chunk lane of v)
-  uint32_t cnt[32];       // matches of the edge
-  uint32_t erun[32];      // listing: triples of the edge written so far
-  int64_t ebase[32];      // listing: output offset of the edge
+// Each kernel keeps only the fields it reads: shared memory and the L1 cache
+// share one array per SM, and the tile kernel's candidate reads live in L1.
+struct HashBatch {  // block and hub kernels
+  static constexpr bool kTile = false, kWrite = false;
+  int64_t beg[32];                  // short list: start of N_u minus its flattened offset; long list: start of N_u
+  uint32_t cnt[32];                 // matches of the edge
   alignas(4) uint8_t own[kOwnCap];  // flattened position -> edge, short lists
+};
+
+struct TileBatch {  // tile kernel, counting passes
+  static constexpr bool kTile = true, kWrite = false;
+  uint64_t pk[32];    // byte address of the list's first flattened position below bit 58, filter salt above
+  int32_t lo[32];     // N_v's slice [lo, lo + len) of the tile
+  int32_t len[32];
+  int32_t salt[32];   // filter salt (chunk lane of v)
+  uint32_t cnt[32];   // matches of the edge
+  alignas(4) uint8_t own[kOwnCap];
+};
+
+struct TileWriteBatch {  // tile kernel, listing write pass
+  static constexpr bool kTile = true, kWrite = true;
+  uint64_t pk[32];
+  int64_t ebase[32];  // output offset of the edge
+  int32_t lo[32];
+  int32_t len[32];
+  int32_t salt[32];
+  uint32_t cnt[32];
+  int32_t u[32];
+  uint32_t erun[32];  // triples of the edge written so far
+  alignas(4) uint8_t own[kOwnCap];
 };
 
 // Fills the batch record for this lane's edge; *tot is the flattened length of
@@ -158,7 +180,8 @@ struct BatchSmem {
 // and more than N_v's dv is left to the hub kernel, which hashes N_u once for
 // all such edges of u and walks the shorter N_v instead; hub_mode 2 also
 // records the edge (per-hub count, flag on the apex vapex).
-__device__ __forceinline__ void batch_setup(BatchSmem& bs, const CountArgs& a, const CountWs& ws, int32_t u,
+template <class BS>
+__device__ __forceinline__ void batch_setup(BS& bs, const CountArgs& a, const CountWs& ws, int32_t u,
                                             bool act, int64_t eg, int32_t salt, int32_t lo, int32_t vlen,
                                             int& tot, bool& is_short, int32_t& len, uint32_t* err, bool list_write,
                                             uint32_t erun0, int32_t vapex, int32_t dv, int hub_mode,
@@ -185,15 +208,22 @@ __device__ __forceinline__ void batch_setup(BatchSmem& bs, const CountArgs& a, c
   const int32_t excl = incl - slen;
   if (excl_out) *excl_out = excl;
   __syncwarp();
-  bs.beg[lane] = is_short ? ub - excl : ub;
-  bs.u[lane] = u;
-  bs.lo[lane] = lo;
-  bs.len[lane] = vlen;
-  bs.salt[lane] = salt;
-  bs.pk[lane] = static_cast<uint64_t>((is_short ? ub - excl : ub) + kBegBias) | (static_cast<uint64_t>(salt) << 58);
+  if constexpr (BS::kTile) {
+    bs.lo[lane] = lo;
+    bs.len[lane] = vlen;
+    bs.salt[lane] = salt;
+    // address arithmetic in uint64 (a short list's start may lie below cols by up to its flattened offset)
+    bs.pk[lane] = (reinterpret_cast<uintptr_t>(a.cols) + 4u * static_cast<uint64_t>(is_short ? ub - excl : ub)) |
+                  (static_cast<uint64_t>(salt) << 58);
+  } else {
+    bs.beg[lane] = is_short ? ub - excl : ub;
+  }
   bs.cnt[lane] = 0;
-  bs.erun[lane] = erun0;
-  if (list_write) bs.ebase[lane] = act ? ws.eoff[eg] : 0;
+  if constexpr (BS::kWrite) {
+    bs.u[lane] = u;
+    bs.erun[lane] = erun0;
+    bs.ebase[lane] = act ? ws.eoff[eg] : 0;
+  }
   // owner table: this lane's byte range [excl, excl + slen), whole 32-bit words
   // where they fit in the range (no other lane writes those words), bytes at the ends
   int32_t i = 0;
@@ -218,7 +248,7 @@ __device__ __forceinline__ unsigned run_mask(int key) {
 
 // Listing: write this lane's triple (if f) at its edge's offset plus the
 // edge's running count; lanes of one edge are contiguous and in candidate order.
-__device__ __forceinline__ void write_triples(BatchSmem& bs, bool has, bool f, int s, int32_t v, int32_t w,
+__device__ __forceinline__ void write_triples(TileWriteBatch& bs, bool has, bool f, int s, int32_t v, int32_t w,
                                              const CountArgs& a, const CountWs& ws, uint32_t* err) {
   const int lane = lane_id();
   const unsigned fm = __ballot_sync(FULL, f);
@@ -243,6 +273,7 @@ __device__ __forceinline__ void write_triples(BatchSmem& bs, bool has, bool f, i
 // Tile kernel
 // ---------------------------------------------------------------------------
 
+template <int MODE>
 struct TileSmem {
   int32_t tile[kTile];
   uint32_t bits[(1 << kTileBitsLog2) / 32];
@@ -250,14 +281,14 @@ struct TileSmem {
   uint32_t vcnt[32];   // triangles with apex v (chunk lane)
   int32_t qw[64];      // filter survivors: candidate id ...
   int32_t qs[64];      // ... and its edge
-  BatchSmem bs;
+  std::conditional_t<MODE == MODE_LIST_WRITE, TileWriteBatch, TileBatch> bs;
 };
 
 // Exact check of the first `cnt` queued survivors, with the per-mode effects.
 template <int MODE>
-__device__ __forceinline__ void exact_flush(TileSmem& sm, int cnt, int top, int32_t vbase, const CountArgs& a,
+__device__ __forceinline__ void exact_flush(TileSmem<MODE>& sm, int cnt, int top, int32_t vbase, const CountArgs& a,
                                             const CountWs& ws, uint32_t* err) {
-  BatchSmem& bs = sm.bs;
+  auto& bs = sm.bs;
   const int lane = lane_id();
   __syncwarp();
   const bool has = lane < cnt;
@@ -268,15 +299,14 @@ __device__ __forceinline__ void exact_flush(TileSmem& sm, int cnt, int top, int3
     atomicAdd(&bs.cnt[s], 1u);
     if (MODE == MODE_LOCAL) atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + w), 1ull);
   }
-  if (MODE == MODE_LIST_WRITE) write_triples(bs, has, f, s, vbase + bs.salt[s], w, a, ws, err);
+  if constexpr (MODE == MODE_LIST_WRITE) write_triples(bs, has, f, s, vbase + bs.salt[s], w, a, ws, err);
   __syncwarp();
 }
 
 // Queue this window's survivors; check 32 of them once 32 are waiting.
 template <int MODE>
-__device__ __forceinline__ void push(TileSmem& sm, bool pass, int32_t w, int s, int& qn, int top, int32_t vbase,
+__device__ __forceinline__ void push(TileSmem<MODE>& sm, bool pass, int32_t w, int s, int& qn, int top, int32_t vbase,
                                      const CountArgs& a, const CountWs& ws, uint32_t* err) {
-  BatchSmem& bs = sm.bs;
   const int lane = lane_id();
   const unsigned m = __ballot_sync(FULL, pass);
   if (!m) return;
@@ -306,10 +336,10 @@ __device__ __forceinline__ void push(TileSmem& sm, bool pass, int32_t w, int s, 
 
 // One batch of the tile's edges; returns the matches of this lane's edge.
 template <int MODE>
-__device__ __forceinline__ uint32_t tile_batch(TileSmem& sm, int top, int32_t u, bool act, int64_t eg, int32_t vl,
+__device__ __forceinline__ uint32_t tile_batch(TileSmem<MODE>& sm, int top, int32_t u, bool act, int64_t eg, int32_t vl,
                                                int32_t lo, int32_t vlen, int32_t vbase, const CountArgs& a,
                                                const CountWs& ws, uint32_t* err) {
-  BatchSmem& bs = sm.bs;
+  auto& bs = sm.bs;
   const int lane = lane_id();
   int tot;
   bool is_short;
@@ -319,7 +349,7 @@ __device__ __forceinline__ uint32_t tile_batch(TileSmem& sm, int top, int32_t u,
   int qn = 0;
   for (int32_t p0 = 0; p0 < tot; p0 += 32 * kTileUnroll) {
     int32_t w[kTileUnroll];
-    int ss[kTileUnroll];  // edge (low 8 bits) and its filter salt (above)
+    uint32_t ss[kTileUnroll];  // edge (bits 0..4) and its filter salt << 26 (bits 26..30)
 #pragma unroll
     for (int k = 0; k < kTileUnroll; ++k) {
       const int32_t p = p0 + 32 * k + lane;
@@ -328,30 +358,30 @@ __device__ __forceinline__ uint32_t tile_batch(TileSmem& sm, int top, int32_t u,
       if (p < tot) {
         const int s = bs.own[p];
         const uint64_t pk = bs.pk[s];
-        w[k] = a.cols[static_cast<int64_t>(pk & kBegMask) - kBegBias + p];
-        ss[k] = s | static_cast<int>(pk >> 58) << 8;
+        w[k] = __ldca(reinterpret_cast<const int32_t*>(pk & kPtrMask) + p);
+        ss[k] = static_cast<uint32_t>(s) | (static_cast<uint32_t>(pk >> 32) & kSaltMix);
       }
     }
 #pragma unroll
     for (int k = 0; k < kTileUnroll; ++k) {
       const int32_t p = p0 + 32 * k + lane;
-      const bool pass = p < tot && ftest<kTileBitsLog2>(sm.bits, w[k], ss[k] >> 8);
-      push<MODE>(sm, pass, w[k], ss[k] & 0xff, qn, top, vbase, a, ws, err);
+      const bool pass = p < tot && ftest<kTileBitsLog2>(sm.bits, w[k], ss[k] & kSaltMix);
+      push<MODE>(sm, pass, w[k], static_cast<int>(ss[k] & 31u), qn, top, vbase, a, ws, err);
     }
   }
   unsigned lm = __ballot_sync(FULL, len > 0 && !is_short);
   while (lm) {
     const int e = __ffs(lm) - 1;
     lm &= lm - 1;
-    const int64_t b = bs.beg[e];
+    const int32_t* lb = reinterpret_cast<const int32_t*>(bs.pk[e] & kPtrMask);  // N_u
     const int32_t le = __shfl_sync(FULL, len, e);
-    const int32_t se = bs.salt[e];
+    const uint32_t se = static_cast<uint32_t>(bs.salt[e]) << 26;
     for (int32_t p0 = 0; p0 < le; p0 += 32 * kTileUnroll) {
       int32_t w[kTileUnroll];
 #pragma unroll
       for (int k = 0; k < kTileUnroll; ++k) {
         const int32_t p = p0 + 32 * k + lane;
-        w[k] = p < le ? a.cols[b + p] : 0;
+        w[k] = p < le ? __ldca(lb + p) : 0;
       }
 #pragma unroll
       for (int k = 0; k < kTileUnroll; ++k) {
@@ -385,10 +415,10 @@ __device__ __forceinline__ void add_graph_totals(const CountArgs& a, bool in_gro
 
 template <int MODE>
 __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, CountWs ws, uint32_t* err) {
-  __shared__ TileSmem s_t[kTileWarps];
+  __shared__ TileSmem<MODE> s_t[kTileWarps];
   __shared__ unsigned long long s_sum[kTileWarps];
   const int lane = lane_id(), wid = threadIdx.x >> 5;
-  TileSmem& sm = s_t[wid];
+  TileSmem<MODE>& sm = s_t[wid];
   unsigned long long acc = 0;
   for (int32_t chunk = 0; a.tile_quota <= 0 || chunk < a.tile_quota; ++chunk) {
     uint32_t off = 0;
@@ -454,7 +484,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, 
         continue;
       }
       __syncwarp();
-      for (int i = 0; i < glen; ++i) fset<kTileBitsLog2>(sm.bits, sm.tile[lo + i], lane);
+      for (int i = 0; i < glen; ++i) fset<kTileBitsLog2>(sm.bits, sm.tile[lo + i], static_cast<uint32_t>(lane) << 26);
       const int maxlen = __reduce_max_sync(FULL, glen);
       const int top = maxlen > 0 ? 1 << (31 - __clz(maxlen)) : 0;
       __syncwarp();
@@ -588,7 +618,7 @@ __device__ __forceinline__ int table_find(const int32_t* tab, int32_t w, bool li
 // Counting passes of the hash kernels: a match adds to its edge (and, for
 // per-vertex counts, to the slot of w, flushed once per chunk).
 template <int MODE>
-__device__ __forceinline__ void hash_record(BatchSmem& bs, uint32_t* slot_cnt, int slot, int s) {
+__device__ __forceinline__ void hash_record(HashBatch& bs, uint32_t* slot_cnt, int slot, int s) {
   if (slot >= 0) {
     atomicAdd(&bs.cnt[s], 1u);
     if (MODE == MODE_LOCAL) atomicAdd(&slot_cnt[slot], 1u);
@@ -657,7 +687,7 @@ __device__ __forceinline__ void emit_long(bool f, int32_t w, int32_t u_e, int32_
 // walking N_u; hub kernel (HUB), edges (x, v) with x on this lane, walking N_x.
 // eg is the lane's edge (its position in cols).  Returns the lane's matches.
 template <int MODE, bool HUB>
-__device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab, uint32_t* slot_cnt, int32_t lo,
+__device__ __forceinline__ uint32_t hash_batch(HashBatch& bs, const int32_t* tab, uint32_t* slot_cnt, int32_t lo,
                                                int32_t hi, int32_t u, bool act, int64_t eg, int32_t v,
                                                const CountArgs& a, const CountWs& ws, uint32_t* err,
                                                bool chunked, bool first_chunk, int32_t dv, bool linear) {
@@ -692,7 +722,6 @@ __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab
     }
 #pragma unroll
     for (int k = 0; k < kUnroll; ++k) {
-      const int32_t p = p0 + 32 * k + lane;
       const int slot = (w[k] >= lo && w[k] <= hi) ? table_find<L>(tab, w[k], linear) : -1;
       if (kWrite) emit_short<HUB>(slot >= 0, s[k], w[k], p0 + 32 * k, excl, slen, u, v, wbase, a, err);
       else hash_record<MODE>(bs, slot_cnt, slot, s[k]);
@@ -715,7 +744,6 @@ __device__ __forceinline__ uint32_t hash_batch(BatchSmem& bs, const int32_t* tab
       }
 #pragma unroll
       for (int k = 0; k < kUnroll; ++k) {
-        const int32_t p = p0 + 32 * k + lane;
         const int slot = (w[k] >= lo && w[k] <= hi) ? table_find<L>(tab, w[k], linear) : -1;
         if (kWrite) emit_long<HUB>(slot >= 0, w[k], u_e, v, base_e, a, err);
         else hash_record<MODE>(bs, slot_cnt, slot, e);
@@ -739,7 +767,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
   using H = HashCfg<MODE>;
   extern __shared__ int32_t tab[];
   uint32_t* slot_cnt = reinterpret_cast<uint32_t*>(tab + H::kSlots);  // LOCAL only
-  __shared__ BatchSmem s_b[kBlockWarps];
+  __shared__ HashBatch s_b[kBlockWarps];
   __shared__ unsigned long long s_red[kBlockWarps];
   __shared__ int64_t s_next;  // next batch of walked lists (warps take batches as they finish)
   const int lane = lane_id(), wid = threadIdx.x >> 5;
@@ -1084,6 +1112,8 @@ cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a_in, CountW
   CountArgs a = a_in;
   if (a.v_hi < 0) a.v_hi = a.n;
   if (a.v_lo < 0 || a.v_lo > a.v_hi || a.v_hi > a.n) return cudaErrorInvalidValue;
+  // the tile kernel packs a byte address of cols below bit 58 (virtual addresses are far narrower)
+  if ((reinterpret_cast<uintptr_t>(a.cols) + 4u * static_cast<uint64_t>(a.m)) >> 58) return cudaErrorInvalidValue;
   a.tile_max = (ctx->tile_max > 0 && ctx->tile_max < kTile) ? ctx->tile_max : kTile;
   a.tile_quota = ctx->tile_quota;
   if (ws.off32 && a.m < (int64_t(1) << 31) - 1) a.off32 = ws.off32;  // filled by launch_mode
