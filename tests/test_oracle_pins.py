@@ -218,6 +218,30 @@ def test_relabelling_invariance(seed):
     assert np.array_equal(brute.canon(perm[a["tri"]]), brute.canon(b["tri"]))
 
 
+def test_orientation_worked_by_hand():
+    # Eq. (1): u precedes v iff d_u < d_v, or d_u = d_v and u < v.  Lists and
+    # listed triples below are worked out by hand from that definition; each
+    # graph has degree ties, so a tie broken the other way changes the answer.
+    k4 = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+    cases = [
+        # path 0-1-2: d = (1, 2, 1), order 0, 2, 1
+        (3, [(0, 1), (1, 2)], [[1], [], [1]], []),
+        # K4: all d = 3, order 0, 1, 2, 3
+        (4, k4, [[1, 2, 3], [2, 3], [3], []], [(0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)]),
+        # triangle 0-1-2 with a pendant on 2: d = (2, 2, 3, 1), order 3, 0, 1, 2
+        (4, [(0, 1), (1, 2), (0, 2), (2, 3)], [[1, 2], [2], [], [2]], [(0, 1, 2)]),
+        # triangle 0-1-2 with a pendant on 0: d = (3, 2, 2, 1), order 3, 1, 2, 0
+        (4, [(0, 1), (1, 2), (0, 2), (0, 3)], [[], [0, 2], [0], [0]], [(1, 2, 0)]),
+    ]
+    for n, e, lists, tris in cases:
+        adj = oracle.Adjacency(n, np.array(e, np.int32))
+        off, cols, dhat = adj.orient()
+        assert [cols[off[v]:off[v + 1]].tolist() for v in range(n)] == lists
+        assert dhat.tolist() == [len(x) for x in lists]
+        # NodeIterator++ lists each triangle as (v, u, w) with v < u < w in the order
+        assert sorted(map(tuple, adj.count(listing=True)["tri"].tolist())) == sorted(tris)
+
+
 @pytest.mark.parametrize("seed", range(3))
 def test_degree_order_minimises_cost(seed):
     # Theorem 3: sum_v d_v * dhat_v is smallest under the degree order.
@@ -408,6 +432,22 @@ def test_part_coin_reduces_to_the_plain_coin_and_to_philox():
         x = oracle.philox([min(a, b), max(a, b), part, 0], [seed & 0xFFFFFFFF, seed >> 32])
         r = (int(x[0]) << 21) | (int(x[1]) >> 11)  # top 53 bits of x0:x1
         assert oracle.sparsify_keep_part(a, b, seed, q, part) == (r * 2.0 ** -53 < q)
+
+
+def test_coin_switches_exactly_at_its_53_bit_value():
+    # the coin keeps an edge iff r * 2^-53 < q, r the top 53 bits of Philox's
+    # words x0:x1: at q = r * 2^-53 (exact in a double) it drops the edge and at
+    # q = (r + 1) * 2^-53 it keeps it, for every part
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        a, b = (int(x) for x in rng.integers(0, 1 << 30, 2))
+        if a == b:
+            continue
+        seed, part = int(rng.integers(0, 1 << 62)), int(rng.integers(0, 1 << 20))
+        x = oracle.philox([min(a, b), max(a, b), part, 0], [seed & 0xFFFFFFFF, seed >> 32])
+        r = (int(x[0]) << 21) | (int(x[1]) >> 11)
+        assert not oracle.sparsify_keep_part(a, b, seed, r * 2.0 ** -53, part)
+        assert oracle.sparsify_keep_part(a, b, seed, (r + 1) * 2.0 ** -53, part)
 
 
 def test_parts_with_q_one_sum_to_t():
