@@ -13,10 +13,11 @@
 // variant keeps the coin to two 32x32->64 products per round; the 64-bit one
 // spends about four times the integer issue slots on emulated 64-bit products.
 //
-// GB300 mapping: a warp takes 32 consecutive vertices, whose lists are one
-// contiguous run of cols; lanes walk that run 32 ids at a time (coalesced), and
-// find their source vertex by a 5-step search over the 32 list starts.
-//   k_mark     coin per oriented edge -> keep[] bytes and kept count per vertex
+// GB300 mapping: consecutive vertices' lists are one contiguous run of cols,
+// which a warp walks 32 ids at a time (coalesced).
+//   k_mark     a warp takes 32 vertices; lanes find the source vertex of their
+//              id by a 5-step search over the 32 list starts and write the
+//              coin of the oriented edge (keep[] byte) and kept counts per vertex
 //   scan       kept counts -> kept CSR offsets
 //   k_compact  copy the kept ids, order preserved, into the kept CSR (a
 //              stream compaction over runs of 64 vertices' lists)
