@@ -35,11 +35,13 @@ def shape_class(g) -> str:
 
 
 def load_table(path: str = TABLE_PATH) -> dict:
+    """The recorded thresholds by shape class; empty when the file is missing or not a JSON object."""
     try:
         with open(path) as f:
-            return json.load(f)
+            table = json.load(f)
     except (OSError, ValueError):
         return {}
+    return table if isinstance(table, dict) else {}
 
 
 def save_table(table: dict, path: str = TABLE_PATH):
