@@ -126,8 +126,14 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        lo, hi = self.window if self.window else (0, 1e18)
-        rows = [s for t, s in self.samples if lo - 0.15 <= t <= hi + 0.15] or [s for _, s in self.samples[-3:]]
+        return self.summarize(self.samples, self.window)
+
+    @staticmethod
+    def summarize(samples, window):
+        """Median SM clock, max clock and active throttle reasons of the (time, csv line)
+        samples taken inside the window (with 0.15 s of slack), else of the last three."""
+        lo, hi = window if window else (0, 1e18)
+        rows = [s for t, s in samples if lo - 0.15 <= t <= hi + 0.15] or [s for _, s in samples[-3:]]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:

@@ -49,3 +49,27 @@ def test_gpu_arm_fails_loudly_without_a_gpu():
     assert r.returncode != 0
     # no measurement line: there is no CPU fallback for the CUDA path
     assert not any(ln.strip().startswith("{") for ln in r.stdout.splitlines())
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_clock_summary_of_nvidia_smi_rows():
+    bench = _bench_module()
+    quiet = "2070, 2070, 910.2, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"
+    capped = "1965, 2070, 1399.8, 0x0000000000000004, Not Active, Not Active, Not Active, Active"
+    hot = "1500, 2070, 1200.0, 0x0000000000000040, Not Active, Active, Not Active, Not Active"
+    samples = [(0.0, hot), (1.0, quiet), (1.1, capped), (1.2, quiet), (1.3, "garbage"), (1.35, "[N/A], 2070"),
+               (5.0, hot)]
+    # only the rows inside the timed window (1.0 .. 1.3, with 0.15 s of slack) count
+    s = bench.ClockSampler.summarize(samples, (1.0, 1.3))
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    # a window with no rows falls back to the last three samples
+    s = bench.ClockSampler.summarize(samples, (10.0, 11.0))
+    assert s["reasons"] == ["hw_thermal_slowdown"] and s["samples"] == 1
+    assert bench.ClockSampler.summarize([], None) is None
