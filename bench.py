@@ -7,11 +7,12 @@ counts, clustering coefficients and the two-pass triangle list (tc_analyze),
 and edge sparsification at q = 0.1 (tc_sparsify_count).  The metric is oriented edges per second (m per step),
 with the intersection kernel's achieved fraction of the measured HBM roofline.
 
-Default workload: preferential attachment PA(n = 2^24, 16 edges per new
-vertex), ~268M undirected edges (edge list 2.1 GB, larger than L2, so no L2
-flush is needed between steps).
+Default workload (the headline): preferential attachment PA(n = 2^27, 16
+edges per new vertex), ~2.15G undirected edges (edge list 17.2 GB, larger
+than L2, so no L2 flush is needed between steps).  The same line carries the
+same measurement for PA(n = 2^24) and R-MAT scale 24 under "workloads".
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload ba24|ba27|rmat24|er]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload ba27|ba24|rmat24|er] [--also ba24,rmat24]
     python bench.py --impl reference   # the CPU oracle on a bounded sample
 Multi-GPU (torchrun, one rank per GPU): each rank counts its own independent
 graph (different seed); no collective on the data path (weak scaling).
@@ -391,19 +392,39 @@ def bench_host_resident(tc, ctx, g, T, dev):
             "csr_bytes": 8 * (g.n + 1) + 4 * g.m + 8 * g.n}
 
 
+SIZE_CLASSES = (("small", 1 << 21), ("medium", 1 << 25), ("large", 1 << 62))
+
+
+def size_class(m: int) -> str:
+    """Requests are grouped by their graph's edge count: small (m <= 2^21, the server's
+    high-priority class by default), medium (m <= 2^25), large."""
+    for name, top in SIZE_CLASSES:
+        if m <= top:
+            return name
+    return "large"
+
+
 def serving_pool():
     """The serving configuration's graph pool (seeded): ER n = 2^12..2^18 with mean
-    degree 16, R-MAT scale 16..20 with edge factor 16, Chung-Lu (gamma 2.1) with
+    degree 16, R-MAT scale 16..24 with edge factor 16, Chung-Lu (gamma 2.1) with
     n = 1e4..1e6 and mean degree 16."""
     import synth
     pool = []
     for lg in (12, 14, 16, 18):
         pool.append((f"ER n=2^{lg}", 1 << lg, synth.er(1 << lg, 8 << lg, 100 + lg)))
-    for sc in (16, 18, 20):
+    for sc in (16, 18, 20, 22, 24):
         pool.append((f"R-MAT scale {sc}", 1 << sc, synth.rmat(sc, 16, 200 + sc)))
     for n in (10 ** 4, 10 ** 5, 10 ** 6):
         pool.append((f"Chung-Lu n={n}", n, synth.chung_lu(n, 16.0, 2.1, 300, n)))
     return pool
+
+
+def request_weights(ms) -> np.ndarray:
+    """Probability that a request targets each graph: proportional to m^(-1/2), so that
+    most requests hit small graphs while each of the largest still gets dozens per
+    10,000 (R-MAT scale 24 about 0.4%)."""
+    w = np.array([1.0 / np.sqrt(max(m, 1)) for m in ms])
+    return w / w.sum()
 
 
 def bench_serving(tc, dev, args):
@@ -416,28 +437,36 @@ def bench_serving(tc, dev, args):
     graphs = serving_pool()
     gids = [srv.add_graph(n, e) for _, n, e in graphs]
     m_of = {gid: len(e) for gid, (_, _, e) in zip(gids, graphs)}
+    class_of = {gid: size_class(len(e)) for gid, (_, _, e) in zip(gids, graphs)}
+    pg = request_weights([len(e) for _, _, e in graphs])
     kinds_p = [0.6, 0.3, 0.1]
     # capacity: mean service time of the mix, one request at a time
     service = {}
     for gid in gids:
         for kind in range(3):
-            srv.wait(srv.submit(gid, kind), copy=False)
+            srv.wait(srv.submit(gid, kind), timeout_ms=600000, copy=False)
             t0 = time.perf_counter()
-            for _ in range(3):
-                srv.wait(srv.submit(gid, kind), copy=False)
-            service[(gid, kind)] = (time.perf_counter() - t0) / 3
-    mean_service = sum(kinds_p[k] * service[(g, k)] for g in gids for k in range(3)) / len(gids)
+            for _ in range(2):
+                srv.wait(srv.submit(gid, kind), timeout_ms=600000, copy=False)
+            service[(gid, kind)] = (time.perf_counter() - t0) / 2
+    mean_service = sum(pg[i] * kinds_p[k] * service[(g, k)] for i, g in enumerate(gids) for k in range(3))
     capacity = 1.0 / mean_service
     out = {"workload": "; ".join(name for name, _, _ in graphs), "pool_gb": pool_bytes / 1e9, "slots": 8,
-           "mix": "60% count, 30% local (T_v, C_v), 10% list", "sequential_capacity_rps": capacity, "rates": []}
+           "mix": "60% count, 30% local (T_v, C_v), 10% list",
+           "graph_choice": "probability proportional to m^(-1/2)",
+           "request_share": {name: round(float(p), 5) for (name, _, _), p in zip(graphs, pg)},
+           "size_classes": "small m <= 2^21, medium m <= 2^25, large above",
+           "service_ms": {f"{name}/{('count', 'local', 'list')[k]}": round(service[(gid, k)] * 1e3, 3)
+                          for (name, _, _), gid in zip(graphs, gids) for k in range(3)},
+           "sequential_capacity_rps": capacity, "rates": []}
     for li, load in enumerate(float(x) for x in args.serve_loads.split(",")):
         rate = load * capacity
         warm = 500
-        total = warm + (args.serve_requests if li == 0 else max(args.serve_requests // 2, 1000))
+        total = warm + args.serve_requests
         rng = np.random.default_rng(1000 + li)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, total))
         kinds = rng.choice(3, total, p=kinds_p)
-        which = rng.integers(0, len(gids), total)
+        which = rng.choice(len(gids), total, p=pg)
         tickets = [None] * total
         ready = threading.Semaphore(0)
         t_start = time.perf_counter()
@@ -457,7 +486,8 @@ def bench_serving(tc, dev, args):
         th = threading.Thread(target=submitter)
         th.start()
         lat, lat_kind, edges, statuses = [], {0: [], 1: [], 2: []}, 0, {}
-        t_first = t_last = None
+        lat_class = {name: [] for name, _ in SIZE_CLASSES}
+        t_first = None
         for i in range(total):
             ready.acquire()
             tk, t_sub = tickets[i]
@@ -468,18 +498,22 @@ def bench_serving(tc, dev, args):
                     t_first = t_sub
                 lat.append(r.latency_ms)
                 lat_kind[r.kind].append(r.latency_ms)
+                lat_class[class_of[r.graph_id]].append(r.latency_ms)
                 edges += m_of[r.graph_id]
         th.join()
         t_last = time.perf_counter()
         span = t_last - t_first
         la = np.array(lat)
+
+        def pct(v, p):
+            return float(np.percentile(v, p)) if v else None
         out["rates"].append({
             "offered_rps": rate, "load": load, "requests": len(lat), "achieved_rps": len(lat) / span,
             "p50_ms": float(np.percentile(la, 50)), "p99_ms": float(np.percentile(la, 99)),
-            "p50_ms_by_kind": {k: float(np.percentile(v, 50)) for k, v in zip(("count", "local", "list"),
-                                                                                lat_kind.values()) if v},
-            "p99_ms_by_kind": {k: float(np.percentile(v, 99)) for k, v in zip(("count", "local", "list"),
-                                                                                lat_kind.values()) if v},
+            "p50_ms_by_kind": {k: pct(v, 50) for k, v in zip(("count", "local", "list"), lat_kind.values()) if v},
+            "p99_ms_by_kind": {k: pct(v, 99) for k, v in zip(("count", "local", "list"), lat_kind.values()) if v},
+            "by_size_class": {c: {"requests": len(v), "p50_ms": pct(v, 50), "p99_ms": pct(v, 99)}
+                              for c, v in lat_class.items() if v},
             "edges_per_s": edges / span, "statuses": {str(k): v for k, v in statuses.items()}})
     out["stats"] = srv.stats()
     srv.close()
@@ -520,24 +554,29 @@ def job_throughput(units_all_ranks: int, ms_slowest: float) -> float:
     return units_all_ranks / (ms_slowest * 1e-3)
 
 
-def run_e2e(args, tc, ctx, dev, edges_host, n, T, q, seed, tri_buf, barrier, world):
+def run_e2e(args, tc, ctx, dev, edges_host, n, T, q, seed, tri_buf, barrier, world, steps):
     """The step end to end through the public API: H2D of the edge list and D2H of
-    T_v, C_v and the listing inside the timed region.  Returns ms per step (max over ranks)."""
+    T_v, C_v, the sparsified count and the listing inside the timed region.  The
+    listing comes back through a page-locked staging buffer of at most 2 GiB, chunk
+    by chunk (a 10^10-triple listing is larger than the host's memory).  Returns
+    (ms per step, max over ranks; H2D bytes; D2H bytes)."""
     import torch
-    import torch.distributed as dist
     stream = torch.cuda.current_stream(dev)
     tv_host = torch.empty(n, dtype=torch.int64).pin_memory()
     cc_host = torch.empty(n, dtype=torch.float64).pin_memory()
-    tri_host = torch.empty((max(T, 1), 3), dtype=torch.int32).pin_memory()
+    stage_rows = max(1, min(T, (2 << 30) // 12))
+    tri_host = torch.empty((stage_rows, 3), dtype=torch.int32).pin_memory()
 
     def one():
         ed = edges_host.to(dev, non_blocking=True)
         g2 = tc.orient(ed, n, ctx)
         T2, tv2, cc2, tri2 = tc.analyze(g2, True, tri_buf[0], ctx)
-        tc.sparsify_count(g2, q, seed, ctx)
+        tc.sparsify_count(g2, q, seed, ctx)  # its two counts come back to the host inside the call
         tv_host.copy_(tv2, non_blocking=True)
         cc_host.copy_(cc2, non_blocking=True)
-        tri_host[: len(tri2)].copy_(tri2, non_blocking=True)
+        for s0 in range(0, len(tri2), stage_rows):
+            r = min(stage_rows, len(tri2) - s0)
+            tri_host[:r].copy_(tri2[s0:s0 + r], non_blocking=True)
         torch.cuda.current_stream(dev).synchronize()
 
     one()  # untimed: the caching allocator takes this path's device buffers once
@@ -545,12 +584,144 @@ def run_e2e(args, tc, ctx, dev, edges_host, n, T, q, seed, tri_buf, barrier, wor
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.e2e_steps):
+    for _ in range(steps):
         one()
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
-    return max_over_ranks(e2e_ms, dev, world)
+    e2e_ms = e0.elapsed_time(e1) / steps
+    h2d = int(edges_host.numel()) * 4
+    d2h = 16 * n + 12 * T + 8 + 16  # T_v, C_v, the listing, T, and the two sparsified counts
+    return max_over_ranks(e2e_ms, dev, world), h2d, d2h
+
+
+def gpu_identity(torch, dev, local_rank):
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        return gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
+    except Exception:
+        return str(local_rank)
+
+
+ORIENT_STAGES = ("orient.degree", "orient.orient_count", "orient.scan", "orient.scatter", "orient.sort_small",
+                 "orient.sort_mid", "orient.sort_big")
+LOCAL_STAGES = ("local.prep", "local.tile", "local.block", "local.hub")
+
+
+def measure_workload(args, tc, ctx, dev, name, steps, warmup, e2e_steps, world, rank, local_rank, barrier,
+                     keep=False):
+    """One workload: W untimed steps, the thresholds autotuned on the per-vertex pass,
+    then K timed steps on the device (CUDA events, clocks sampled), then the e2e steps.
+    Returns (record, state); state holds the graph for the side studies when keep."""
+    import torch
+    w = WORKLOADS[name]
+    n, e_np = make_graph(w, replica_seed(args.seed, rank))
+    m = len(e_np)
+    edges_host = torch.from_numpy(e_np).pin_memory()
+    del e_np
+    edges_dev = edges_host.to(dev)
+    q, seed = args.q, args.seed
+    tri_buf = [None]
+
+    def step():
+        g = tc.orient(edges_dev, n, ctx)
+        T, tv, cc, tri = tc.analyze(g, True, tri_buf[0], ctx)
+        tri_buf[0] = tri if tri_buf[0] is None or len(tri) > tri_buf[0].shape[0] else tri_buf[0]
+        sp = tc.sparsify_count(g, q, seed, ctx)
+        return g, T, tv, cc, tri, sp
+
+    ctx.set_tuning(0, 1)
+    ctx.set_hub_min(0)
+    for _ in range(max(warmup, 1)):
+        g, T, tv, cc, tri, sp = step()
+    tuned = None
+    if not args.no_tune:  # pick the cost-bin thresholds on this graph (outside the timed region)
+        from paper_1706_05151_gb300 import autotune
+        # tuned on the per-vertex pass: with the listing write pass it is most of the step
+        best, times, hub, hub_times = autotune.tune(g, ctx, record=False, local=True)
+        tuned = {"tile_max": best, "local_ms_by_tile_max": {str(k): round(v, 3) for k, v in times.items()},
+                 "hub_min": hub, "local_ms_by_hub_min": {str(k): round(v, 3) for k, v in hub_times.items()}}
+        g, T, tv, cc, tri, sp = step()
+    W = int((g.deg.to(torch.int64) * g.dhat.to(torch.int64)).sum().item())
+    assert int(tv.sum().item()) == 3 * T and len(tri) == T
+    del g, tv, cc, tri
+
+    sampler = ClockSampler(gpu_identity(torch, dev, local_rank))
+    time.sleep(0.3)
+    ctx.reset_stats()
+    ctx.set_profiling(True)
+    stream = torch.cuda.current_stream(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.time()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        out = step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    t_wall1 = time.time()
+    ctx.set_profiling(False)
+    launches = ctx.launches
+    stages = ctx.stages()
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / steps, dev, world)
+    sampler.mark(t_wall0, t_wall1)
+    clocks = sampler.stop()
+    g, T, tv, cc, tri, sp = out
+    del out
+
+    e2e = None
+    if e2e_steps > 0:
+        if not keep:
+            del g, tv, cc, tri
+            torch.cuda.empty_cache()
+        e2e_ms, h2d, d2h = run_e2e(args, tc, ctx, dev, edges_host, n, T, q, seed, tri_buf, barrier, world,
+                                   e2e_steps)
+        m_all = sum_over_ranks(m, dev, world)
+        e2e = {"value": job_throughput(m_all, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": e2e_steps,
+               "listing_d2h": "through a page-locked staging buffer of at most 2 GiB, chunk by chunk"}
+    m_total = sum_over_ranks(m, dev, world)
+
+    peak, peak_src = load_peaks()
+    # every kernel of the per-vertex counting pass: preparation (int32 offsets, hub
+    # schedule), tile, block and hub kernels
+    inter_ms = sum(stages.get(k, (0.0, 0))[0] for k in LOCAL_STAGES)
+    inter_calls = max(stages.get("local.tile", (0.0, 0))[1], 1)
+    inter_avg_ms = inter_ms / inter_calls
+    b_alg = 4 * W + 4 * m + 8 * (n + 1)
+    achieved = b_alg / (inter_avg_ms * 1e-3) / 1e9
+    orient_ms = sum(stages.get(k, (0.0, 0))[0] for k in ORIENT_STAGES) / steps
+    b_orient = 8 * m + 4 * m + 8 * (n + 1) + 4 * n
+    rec = {
+        "workload": w["label"], "n": n, "m": m, "triangles": T, "W_sum_d_dhat": W,
+        "value": job_throughput(m_total, ms), "unit": UNIT, "steps": steps, "warmup": warmup,
+        "ms_per_step": ms,
+        "l2": "inputs larger than L2 (edge list %.2f GB, CSR %.2f GB): no flush between steps" % (
+            8 * m / 1e9, (4 * m + 8 * n) / 1e9),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": recorded_traffic("local.tile", name),
+                     "kernel": "k_count_tile+k_count_block+hub side, per-vertex pass of tc_analyze",
+                     "algorithmic_bytes": b_alg, "avg_launch_ms": inter_avg_ms, "peak_source": peak_src},
+        "orient_roofline": {"bound": "hbm", "algorithmic_bytes": b_orient, "avg_launch_ms": orient_ms,
+                            "achieved": b_orient / (orient_ms * 1e-3) / 1e9 if orient_ms else None,
+                            "frac": (b_orient / (orient_ms * 1e-3) / 1e9 / peak) if orient_ms else None,
+                            "unit": "GB/s", "peak": peak},
+        "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "stages_ms_per_step": {k: round(v[0] / steps, 4) for k, v in sorted(stages.items())},
+        "autotune": tuned,
+        "sparsified": {"kept_edges": sp[1], "kept_triangles": sp[0], "estimate": sp[2],
+                       "rel_error": abs(sp[2] - T) / T if T else None},
+    }
+    state = None
+    if keep:
+        state = dict(g=g, T=T, n=n, m=m, edges_dev=edges_dev)
+    else:
+        del edges_dev
+    del edges_host
+    tri_buf.clear()
+    torch.cuda.empty_cache()
+    return rec, state
 
 
 def main():
@@ -559,10 +730,14 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tc", choices=["tc", "reference"])
-    ap.add_argument("--workload", default="ba24", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="ba27", choices=sorted(WORKLOADS))
+    ap.add_argument("--also", default="ba24,rmat24",
+                    help="more workloads measured the same way, reported under 'workloads' (empty: none)")
+    ap.add_argument("--also-steps", type=int, default=5)
     ap.add_argument("--q", type=float, default=0.1)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--also-e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-log-n", type=int, default=20, help="log2 n of the CPU-baseline sample")
     ap.add_argument("--ref-log-n", type=int, default=18, help="log2 n of each reference-arm step")
@@ -604,101 +779,36 @@ def main():
     if world > 1:
         dist.barrier()
     ctx = tc.Context(local_rank)
-    w = WORKLOADS[args.workload]
-    n, e_np = make_graph(w, replica_seed(args.seed, rank))
-    m = len(e_np)
-    edges_host = torch.from_numpy(e_np).pin_memory()
-    edges_dev = edges_host.to(dev)
-    q, seed = args.q, args.seed
-
-    tri_buf = [None]
-
-    def step():
-        g = tc.orient(edges_dev, n, ctx)
-        T, tv, cc, tri = tc.analyze(g, True, tri_buf[0], ctx)
-        tri_buf[0] = tri if tri_buf[0] is None or len(tri) > tri_buf[0].shape[0] else tri_buf[0]
-        sp = tc.sparsify_count(g, q, seed, ctx)
-        return g, T, tv, cc, tri, sp
-
-    for _ in range(args.warmup):
-        g, T, tv, cc, tri, sp = step()
-    tuned = None
-    if not args.no_tune:  # pick the cost-bin threshold on this graph (outside the timed region)
-        from paper_1706_05151_gb300 import autotune
-        # tuned on the per-vertex pass: with the listing write pass it is most of the step
-        best, times, hub, hub_times = autotune.tune(g, ctx, record=False, local=True)
-        tuned = {"tile_max": best, "local_ms_by_tile_max": {str(k): round(v, 3) for k, v in times.items()},
-                 "hub_min": hub, "local_ms_by_hub_min": {str(k): round(v, 3) for k, v in hub_times.items()}}
-        g, T, tv, cc, tri, sp = step()
-    W = int((g.deg.to(torch.int64) * g.dhat.to(torch.int64)).sum().item())
-    assert int(tv.sum().item()) == 3 * T and len(tri) == T
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    gpu_id = None
-    try:
-        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
-        if not gpu_id.startswith("GPU-"):
-            gpu_id = "GPU-" + gpu_id
-    except Exception:
-        gpu_id = str(local_rank)
-    sampler = ClockSampler(gpu_id)
-    time.sleep(0.3)
-
-    # ---- timed region: K device-resident steps ----
-    ctx.reset_stats()
-    ctx.set_profiling(True)
-    stream = torch.cuda.current_stream(dev)
-    barrier()
-    torch.cuda.synchronize(dev)
-    t_wall0 = time.time()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    barrier()
-    t_wall1 = time.time()
-    ctx.set_profiling(False)
-    launches = ctx.launches
-    stages = ctx.stages()
-    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dev, world)
-    sampler.mark(t_wall0, t_wall1)
-    clocks = sampler.stop()
-
-    # ---- e2e: host buffers through the public API, copies inside the timed region ----
-    e2e_ms = None
-    if args.e2e_steps > 0:
-        e2e_ms = run_e2e(args, tc, ctx, dev, edges_host, n, T, q, seed, tri_buf, barrier, world)
-    m_total = sum_over_ranks(m, dev, world)
-
+    head, st = measure_workload(args, tc, ctx, dev, args.workload, args.steps, args.warmup, args.e2e_steps,
+                                world, rank, local_rank, barrier, keep=True)
+    g, T, n, edges_dev = st["g"], st["T"], st["n"], st["edges_dev"]
+    del st
     part = bench_partition(tc, ctx, g, T, dev) if world == 1 and args.partition else None
     orders = bench_orders(tc, ctx, edges_dev, n, T, dev, args.seed) if world == 1 and args.orders else None
-    spacc = bench_sparsify_accuracy(tc, ctx, g, T, dev, q) if world == 1 and args.sparsify_study else None
+    spacc = bench_sparsify_accuracy(tc, ctx, g, T, dev, args.q) if world == 1 and args.sparsify_study else None
     host = bench_host_resident(tc, ctx, g, T, dev) if world == 1 and args.host_study else None
+    del g, edges_dev
+    torch.cuda.empty_cache()
+
+    others = {}
+    for nm in [x for x in args.also.split(",") if x and x != args.workload]:
+        others[nm], _ = measure_workload(args, tc, ctx, dev, nm, args.also_steps, args.warmup,
+                                         args.also_e2e_steps, world, rank, local_rank, barrier)
+    ctx.set_tuning(0, 1)
+    ctx.set_hub_min(0)
 
     batched = None
     if args.batch_graphs > 0:
         batched = bench_batched(tc, ctx, dev, args, rank)
     serving = None
     if args.serve_requests > 0 and world == 1:
-        del g, tv, cc, tri_buf
         torch.cuda.empty_cache()
         serving = bench_serving(tc, dev, args)
-
-    # ---- roofline of the intersection kernel (per-vertex counting pass) ----
-    peak, peak_src = load_peaks()
-    # every kernel of the per-vertex counting pass: preparation (int32 offsets, hub
-    # schedule), tile, block and hub kernels
-    inter_ms = sum(stages.get(k, (0.0, 0))[0] for k in ("local.prep", "local.tile", "local.block", "local.hub"))
-    inter_calls = max(stages.get("local.tile", (0.0, 0))[1], 1)
-    inter_avg_ms = inter_ms / inter_calls
-    b_alg = 4 * W + 4 * m + 8 * (n + 1)
-    achieved = b_alg / (inter_avg_ms * 1e-3) / 1e9
-    traffic = recorded_traffic("local.tile", args.workload)
 
     if rank == 0:
         cpu = None
@@ -706,41 +816,36 @@ def main():
             import synth
             sn = 1 << args.cpu_log_n
             se = synth.ba(sn, 16, args.seed)
-            dt, sm, _ = cpu_oracle_pipeline(sn, se, q, seed)
+            dt, sm, _ = cpu_oracle_pipeline(sn, se, args.q, args.seed)
             cpu = {"value": sm / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"CPU oracle (NodeIterator++, 1 thread) full step on PA(n=2^{args.cpu_log_n}, "
                              f"k=16), m={sm}: adjacency, T, T_v, listing, C_v, sparsified count; {dt:.1f} s"}
-        h2d = 8 * m
-        d2h = 16 * n + 12 * T + 8 * 3
         out = {
-            "metric": METRIC, "value": job_throughput(m_total, ms), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": w["label"], "n": n, "m": m, "triangles": T, "W_sum_d_dhat": W,
-                       "q": q, "seed": args.seed,
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": head["workload"], "n": head["n"], "m": head["m"], "triangles": head["triangles"],
+                       "W_sum_d_dhat": head["W_sum_d_dhat"], "q": args.q, "seed": args.seed,
                        "step": "tc_orient + tc_analyze(T, T_v, C_v, triangle list) + tc_sparsify_count(q)",
-                       "l2": "inputs larger than L2 (edge list %.2f GB, CSR %.2f GB)" % (
-                           8 * m / 1e9, (4 * m + 8 * n) / 1e9),
+                       "l2": head["l2"],
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "autotune": tuned},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_count_tile+k_count_block+hub side, per-vertex pass of tc_analyze",
-                         "algorithmic_bytes": b_alg, "avg_launch_ms": inter_avg_ms, "peak_source": peak_src},
-            "e2e": ({"value": job_throughput(m_total, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms} if e2e_ms else None),
-            "gpu_launches": launches,
-            "clocks": clocks,
-            "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in sorted(stages.items())},
+                       "autotune": head["autotune"]},
+            "roofline": head["roofline"],
+            "orient_roofline": head["orient_roofline"],
+            "e2e": head["e2e"],
+            "gpu_launches": head["gpu_launches"],
+            "clocks": head["clocks"],
+            "stages_ms_per_step": head["stages_ms_per_step"],
             "cpu_baseline": cpu,
+            "workloads": others,
             "partition": part,
             "orders": orders,
             "sparsify_accuracy": spacc,
             "host_resident_csr": host,
             "batched": batched,
             "serving": serving,
-            "sparsified": {"kept_edges": sp[1], "kept_triangles": sp[0], "estimate": sp[2],
-                           "rel_error": abs(sp[2] - T) / T if T else None},
+            "sparsified": head["sparsified"],
         }
         print(json.dumps(out), flush=True)
     if world > 1:

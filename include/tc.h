@@ -499,7 +499,9 @@ tc_status tc_serve_stats(tc_server* s, tc_serve_stats_t* out);
  *   stream     cudaStream_t on the current device (NULL = legacy default stream)
  * The call only enqueues work: read total_dev and check_dev after the stream
  * has finished.  It returns TC_ERR_INVALID_ARG for NULL or negative arguments
- * and TC_ERR_CUDA if a CUDA call fails.  The first call on a device does a
+ * and for misaligned pointers (offsets and total_dev must be 8-byte aligned,
+ * cols and check_dev 4-byte aligned; nothing is enqueued then), and
+ * TC_ERR_CUDA if a CUDA call fails.  The first call on a device does a
  * one-time set-up (it looks up the array's device address), so make that first
  * call before any stream capture begins.  Every call on a device shares the
  * one array and leaves its contents behind (each call clears the cursors it

@@ -232,8 +232,13 @@ class Context:
     def workspace(self, op: int, n: int, m: int) -> torch.Tensor:
         need = self.workspace_size(op, n, m)
         if self._ws is None or self._ws.numel() < need:
+            self._ws = None
             self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
         return self._ws
+
+    def release_workspace(self):
+        """Drop the cached workspace (it is reallocated by the next call that needs one)."""
+        self._ws = None
 
 
 _default_ctx: dict[int, Context] = {}

@@ -55,6 +55,13 @@ extern "C" tc_status tc_count_static(const tc_graph* g, uint64_t* total_dev, uin
   if (!g || !total_dev || !check_dev) return TC_ERR_INVALID_ARG;
   if (g->n < 0 || g->m < 0 || !g->offsets || (g->m > 0 && !g->cols)) return TC_ERR_INVALID_ARG;
   if (g->n > TC_STATIC_MAX_N) return TC_ERR_UNSUPPORTED;
+  // the kernels read offsets as 8-byte words, add into *total_dev with a 64-bit
+  // atomic and set bits of *check_dev with a 32-bit one: a misaligned pointer
+  // would fault on the device, so it is refused here with nothing enqueued
+  auto misaligned = [](const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) != 0; };
+  if (misaligned(g->offsets, 8) || misaligned(total_dev, 8) || misaligned(check_dev, 4) ||
+      (g->cols && misaligned(g->cols, 4)))
+    return TC_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TC_ERR_CUDA;
   void* scratch = nullptr;

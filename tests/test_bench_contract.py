@@ -73,3 +73,14 @@ def test_clock_summary_of_nvidia_smi_rows():
     s = bench.ClockSampler.summarize(samples, (10.0, 11.0))
     assert s["reasons"] == ["hw_thermal_slowdown"] and s["samples"] == 1
     assert bench.ClockSampler.summarize([], None) is None
+
+
+def test_serving_size_classes_and_request_weights():
+    bench = _bench_module()
+    assert bench.size_class(1 << 21) == "small" and bench.size_class((1 << 21) + 1) == "medium"
+    assert bench.size_class(1 << 25) == "medium" and bench.size_class(260_000_000) == "large"
+    ms = [32_768, 1_000_000, 62_000_000, 260_000_000]
+    p = bench.request_weights(ms)
+    assert abs(p.sum() - 1.0) < 1e-12 and all(a > b for a, b in zip(p, p[1:]))
+    # proportional to m^(-1/2): the ratio of two graphs' shares is the root of their sizes' ratio
+    assert abs(p[0] / p[3] - (ms[3] / ms[0]) ** 0.5) < 1e-9

@@ -1,11 +1,11 @@
-"""Parity at the full size of the preferential-attachment configuration, PA(n = 2^24, k = 16).
+"""Exact parity at the full size of the preferential-attachment configuration, PA(n = 2^24, k = 16).
 
-The oracle cannot run NodeIterator++ on 268M edges within a test, so the
-checks are: the whole oriented CSR (the oracle's orientation is one linear
-pass), T_v and C_v on sampled vertices (T_v by its definition, one vertex at a
-time), the sparsified count and kept-edge count (the oracle counts the small
-kept graph), and properties that hold at any size.  The calls are the ones
-bench.py times, with the same launch configuration.
+Everything is compared with a complete oracle result, computed on the host's
+cores by the parallel oracle (oracle/par.py: NodeIteratorN, Figure 2, pinned
+to the serial NodeIterator++ of Figure 1): the whole oriented CSR, T, the
+whole T_v and C_v vectors, the whole triangle list (343,808 triples) and the
+sparsified count.  The calls are the ones bench.py times, with the thresholds
+it picks.
 """
 from __future__ import annotations
 
@@ -15,6 +15,7 @@ import torch
 
 import oracle
 import synth
+from oracle import par
 
 pytestmark = pytest.mark.gpu
 
@@ -34,6 +35,34 @@ def run():
     yield tc, e, g, T, tv, cc, tri
     tc.default_context().set_tuning(0, 1)
     tc.default_context().set_hub_min(0)
+    tc.default_context().release_workspace()
+    del g, tv, cc, tri
+    torch.cuda.empty_cache()
+
+
+@pytest.fixture(scope="module")
+def ref(run):
+    """The oracle's full result on the same edge list."""
+    e = run[1]
+    adj = par.adjacency(N, e)
+    deg = adj.deg
+    off, cols, dhat = par.orient(adj)
+    del adj
+    r = par.count(N, off, cols, local=True, fingerprint=True)
+    r.update(off=off, cols=cols, dhat=dhat, deg=deg)
+    return r
+
+
+def equal_on_device(dev: torch.Tensor, host: np.ndarray, chunk: int = 1 << 28) -> bool:
+    """dev == host element by element, copying the host array up in chunks."""
+    if dev.numel() != host.size:
+        return False
+    flat = dev.reshape(-1)
+    h = host.reshape(-1)
+    for s in range(0, h.size, chunk):
+        if not torch.equal(flat[s:s + chunk], torch.from_numpy(np.ascontiguousarray(h[s:s + chunk])).to(dev.device)):
+            return False
+    return True
 
 
 def rows_strictly_increasing(tri: torch.Tensor, chunk: int = 1 << 27) -> bool:
@@ -62,63 +91,46 @@ def rows_oriented(tri: torch.Tensor, deg: torch.Tensor, chunk: int = 1 << 27) ->
     return True
 
 
-def occurrences(tri: torch.Tensor, v: int, chunk: int = 1 << 27) -> int:
-    return sum(int((tri[s:s + chunk] == v).sum().item()) for s in range(0, tri.shape[0], chunk))
+def apex_counts(tri: torch.Tensor, n: int, chunk: int = 1 << 27) -> torch.Tensor:
+    """Triangles per first vertex of the listing (bincount of column 0, in chunks, on the device)."""
+    c = torch.zeros(n, dtype=torch.int64, device=tri.device)
+    for s in range(0, tri.shape[0], chunk):
+        c += torch.bincount(tri[s:s + chunk, 0].to(torch.int64), minlength=n)
+    return c
 
 
-def test_fullsize_orientation_is_exact(run):
+def test_fullsize_orientation_is_exact(run, ref):
     tc, e, g, *_ = run
-    adj = oracle.Adjacency(N, e)
-    off, cols, dhat = adj.orient()
-    assert np.array_equal(g.offsets.cpu().numpy(), off)
-    assert np.array_equal(g.dhat.cpu().numpy(), dhat)
-    assert np.array_equal(g.deg.cpu().numpy(), adj.deg)
-    assert np.array_equal(g.cols.cpu().numpy(), cols)
-    run_cache["adj"] = adj
+    assert equal_on_device(g.offsets, ref["off"])
+    assert equal_on_device(g.dhat, ref["dhat"])
+    assert equal_on_device(g.deg, ref["deg"])
+    assert equal_on_device(g.cols, ref["cols"])
 
 
-run_cache = {}
-
-
-def test_fullsize_sampled_vertex_counts(run):
+def test_fullsize_counts_are_exact(run, ref):
     tc, e, g, T, tv, cc, tri = run
-    adj = run_cache.get("adj") or oracle.Adjacency(N, e)
-    deg = adj.deg
-    rng = np.random.default_rng(5)
-    sample = rng.choice(N, 400, replace=False)
-    sample = np.concatenate([sample, np.arange(0, 64)])            # the oldest, highest-degree vertices
-    sample = [int(v) for v in sample if deg[v] <= 4000]
-    tv_h = tv.cpu().numpy()
-    cc_h = cc.cpu().numpy()
-    ref_tv = np.array([adj.vertex_triangles(v) for v in sample], dtype=np.int64)
-    assert np.array_equal(tv_h[sample], ref_tv)
-    ref_cc = oracle.clustering(deg[sample], ref_tv)
-    assert np.array_equal(cc_h[sample].view(np.uint64), ref_cc.view(np.uint64))
+    assert T == ref["T"]
+    assert tc.count(g) == ref["T"]
+    assert np.array_equal(tv.cpu().numpy(), ref["tv"])
+    # C_v for every vertex, bit for bit (one correctly rounded division on both sides)
+    ref_cc = oracle.clustering(ref["deg"], ref["tv"])
+    assert np.array_equal(cc.cpu().numpy().view(np.uint64), ref_cc.view(np.uint64))
 
 
-def test_fullsize_invariants(run):
+def test_fullsize_listing_is_exact(run, ref):
     tc, e, g, T, tv, cc, tri = run
-    assert int(tv.sum().item()) == 3 * T
-    assert tc.count(g) == T
-    assert len(tri) == T
-    # every listed triple is a triangle, listed once
+    assert len(tri) == ref["T"]
     assert rows_strictly_increasing(tri)
-    assert int(tri.min().item()) >= 0 and int(tri.max().item()) < N
     assert rows_oriented(tri, g.deg)
-    adj = run_cache.get("adj") or oracle.Adjacency(N, e)
-    idx = np.random.default_rng(6).choice(T, min(T, 20000), replace=False)
-    th = tri[idx].cpu().numpy()
-
-    def has(a, b):
-        lo, hi = adj.off[a], adj.off[a + 1]
-        j = np.searchsorted(adj.adj[lo:hi], b)
-        return j < hi - lo and adj.adj[lo + j] == b
-    assert all(has(a, b) and has(b, c) and has(a, c) for a, b, c in th)
+    ref_tri = par.listing(N, ref["off"], ref["cols"], ref["apex"])
+    got = tri.cpu().numpy()
+    rows = lambda t: t[np.lexsort((t[:, 2], t[:, 1], t[:, 0]))]
+    assert np.array_equal(rows(got), rows(ref_tri))
 
 
-def test_fullsize_sparsified_count(run):
+def test_fullsize_sparsified_count(run, ref):
     tc, e, g, *_ = run
     t, mk, est = tc.sparsify_count(g, 0.1, 1)
-    rt, rmk, rest = oracle.sparsify_count(N, e, 1, 0.1)
+    rt, rmk, rest = par.sparsify_count(N, e, ref["deg"], 1, 0.1)
     assert (t, mk) == (rt, rmk)
     assert est == rest

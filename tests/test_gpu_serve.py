@@ -124,3 +124,31 @@ def test_invalid_requests(tc):
     with pytest.raises(tc.TcError):
         srv.submit(gid, tc.COUNT)
     srv.close()
+
+
+def test_small_requests_unchanged_behind_a_large_one(tc):
+    # an R-MAT scale 22 listing (2.1e9 triples, 25 GB) is running when small requests arrive:
+    # they are admitted beside it, finish first, and return what they return alone
+    big_n, big_e = 1 << 22, synth.rmat(22, 16, 21)
+    srv = tc.Server(48 << 30, slots=6, admit_timeout_ms=120000)
+    big = srv.add_graph(big_n, big_e)
+    smalls = [(1 << 12, synth.er(1 << 12, 8 << 12, 22)), (5000, synth.chung_lu(5000, 16.0, 2.1, 23, 0)),
+              (1 << 12, synth.rmat(12, 16, 24))]
+    sids = [srv.add_graph(n, e) for n, e in smalls]
+    alone = {}
+    for gid, (n, e) in zip(sids, smalls):
+        ref = oracle.count(n, e, local=True, listing=True)
+        for kind in (tc.COUNT, tc.LOCAL, tc.LIST):
+            r = srv.wait(srv.submit(gid, kind))
+            assert r.status == 0 and r.triangles == ref["T"]
+            alone[(gid, kind)] = key_of(r)
+    big_ref = srv.wait(srv.submit(big, tc.COUNT), timeout_ms=120000).triangles
+    big_t = srv.submit(big, tc.LIST)
+    small_t = [(srv.submit(gid, kind), gid, kind) for gid in sids for kind in (tc.COUNT, tc.LOCAL, tc.LIST)]
+    small_res = [(srv.wait(t, timeout_ms=120000), gid, kind) for t, gid, kind in small_t]
+    b = srv.wait(big_t, timeout_ms=300000, copy=False)
+    assert b.status == 0 and b.triangles == big_ref > 10 ** 9
+    for r, gid, kind in small_res:
+        assert key_of(r) == alone[(gid, kind)], (gid, kind)
+        assert r.latency_ms < b.latency_ms  # not held behind the large request
+    srv.close()

@@ -77,7 +77,7 @@ MUTANTS = [
 def _caught(check) -> bool:
     try:
         check()
-    except AssertionError:
+    except (AssertionError, pytest.fail.Exception):  # a failed assert, or pytest.raises that saw nothing
         return True
     return False
 
@@ -96,5 +96,57 @@ def test_planted_mistake_fails_a_pin(what, line, slip, checks, tmp_path, monkeyp
     monkeypatch.setattr(oracle, "_SRC", str(planted))
     monkeypatch.setattr(oracle, "_LIB_PATH", str(lib))
     monkeypatch.setattr(oracle, "_lib", None)
+    caught = [_caught(c) for c in checks]
+    assert any(caught), f"no pin noticed: {what}"
+
+
+# ---- the parallel oracle: each slip must break its equality with the serial oracle ----
+
+from tests import test_oracle_par as par_pins  # noqa: E402
+
+_PAR_GRAPHS = {g[0]: g for g in par_pins.GRAPHS}
+
+
+def _par_equal(*names):
+    return [lambda nm=nm: par_pins.test_parallel_oracle_equals_serial(*_PAR_GRAPHS[nm]) for nm in names]
+
+
+PAR_MUTANTS = [
+    ("T_w share of a triangle dropped (Section 11)",
+     "            per_w[a - lo] += 1;\n", "\n", _par_equal("K9", "rmat9")),
+    ("T_u share of a triangle dropped (Section 11)",
+     "        if (tv && t_e) __atomic_fetch_add(&tv[u], t_e, __ATOMIC_RELAXED);\n", "\n", _par_equal("K9", "rmat9")),
+    ("merge skips the first id of N_v (Figure 2)",
+     "        int64_t a = lo, b = off[u], be = off[u + 1], t_e = 0;\n",
+     "        int64_t a = lo + 1, b = off[u], be = off[u + 1], t_e = 0;\n", _par_equal("K9", "wheel12")),
+    ("order's tie broken by the larger id (Eq. 1)",
+     "  return ku < kv || (ku == kv && u < v);\n", "  return ku < kv || (ku == kv && u > v);\n",
+     _par_equal("K9", "cycle7")),
+    ("repeated edges accepted",
+     "      if (adj[i] == adj[i - 1]) dup = 1;\n", "      ;\n",
+     [lambda: par_pins.test_parallel_adjacency_rejects_non_simple_input([[0, 1], [2, 3], [1, 0]], "repeated")]),
+    ("a fingerprint constant differs from its tensor restatement",
+     "static const uint64_t FP_B[2] = {12345ULL, 1013904223ULL};\n",
+     "static const uint64_t FP_B[2] = {12346ULL, 1013904223ULL};\n", _par_equal("K9")),
+]
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc to build the planted copies")
+@pytest.mark.parametrize("what,line,slip,checks", PAR_MUTANTS, ids=[m[0] for m in PAR_MUTANTS])
+def test_planted_mistake_in_parallel_oracle_fails_a_pin(what, line, slip, checks, tmp_path, monkeypatch):
+    from oracle import par
+    src_par, src_serial = par._SRCS
+    with open(src_par) as f:
+        src = f.read()
+    assert src.count(line) == 1, f"the line to plant in is not unique or missing: {line!r}"
+    planted = tmp_path / "tc_oracle_par.c"
+    planted.write_text(src.replace(line, slip))
+    lib = tmp_path / "liboracle_par_planted.so"
+    subprocess.run(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", str(planted), src_serial, "-o",
+                    str(lib)], check=True)
+    os.utime(lib)
+    monkeypatch.setattr(par, "_SRCS", [str(planted), src_serial])
+    monkeypatch.setattr(par, "_LIB_PATH", str(lib))
+    monkeypatch.setattr(par, "_lib", None)
     caught = [_caught(c) for c in checks]
     assert any(caught), f"no pin noticed: {what}"
