@@ -55,7 +55,8 @@ constexpr int kShortLen = 32;        // N_u shorter than this is walked end to e
 constexpr int kOwnCap = 32 * kShortLen;
 constexpr int kTileUnroll = 8;       // candidate windows in flight per lane, tile kernel
 constexpr int kBlockWarps = 8;       // warps per block, block kernel
-constexpr int kHashBatch = 32;       // walked lists a warp takes at a time (block and hub kernels, <= 32)
+constexpr int kHashBatch = 32;       // walked lists a warp takes at a time (block and hub kernels, <= 32) ...
+constexpr int kMinHashBatch = 4;     // ... and at least, near the end of a chunk
 constexpr uint64_t kPtrMask = (uint64_t(1) << 58) - 1;  // packed list address: byte address below bit 58
 constexpr uint32_t kSaltMix = 0x7C000000u;              // filter salt (0..31) << 26: bits 58..62 of the packed word
 constexpr int kHubMinDefault = 64;   // default hub_min: lists of at least this many ids take their in-edges
@@ -91,8 +92,11 @@ __device__ __forceinline__ int32_t list_bounds(const CountArgs& a, int32_t u, in
     set_err(err, ERR_BAD_ID);
     return 0;
   }
-  // the int32 copy, when there is one, halves the bytes of this random read
-  const int64_t lo = a.off32 ? a.off32[u] : a.offsets[u], hi = a.off32 ? a.off32[u + 1] : a.offsets[u + 1];
+  // the int32 copy, when there is one, halves the bytes of this random read; it is read
+  // about twice per oriented edge, so its lines are the last this kernel lets L2 evict
+  const uint64_t keep = l2_policy_evict_last();
+  const int64_t lo = a.off32 ? ld_nc_hint(a.off32 + u, keep) : ld_nc_hint(a.offsets + u, keep);
+  const int64_t hi = a.off32 ? ld_nc_hint(a.off32 + u + 1, keep) : ld_nc_hint(a.offsets + u + 1, keep);
   if (lo < 0 || hi < lo || hi > a.m) {
     set_err(err, ERR_BAD_CSR);
     return 0;
@@ -420,6 +424,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, 
   const int lane = lane_id(), wid = threadIdx.x >> 5;
   TileSmem<MODE>& sm = s_t[wid];
   unsigned long long acc = 0;
+  const uint64_t stream = l2_policy_evict_first();
   for (int32_t chunk = 0; a.tile_quota <= 0 || chunk < a.tile_quota; ++chunk) {
     uint32_t off = 0;
     if (lane == 0) off = atomicAdd(&ws.counters[kCtrCursor], 32u);
@@ -429,9 +434,9 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, 
     const int32_t v = static_cast<int32_t>(base) + lane;
     const bool valid = v < a.v_hi;
     int64_t b = 0, e = 0;
-    if (valid) {
-      b = a.offsets[v];
-      e = a.offsets[v + 1];
+    if (valid) {  // apex offsets and lists are each read once here: first out of L2
+      b = ld_nc_hint(a.offsets + v, stream);
+      e = ld_nc_hint(a.offsets + v + 1, stream);
       if (b < 0 || e < b || e > a.m) {
         set_err(err, ERR_BAD_CSR);
         b = e = 0;
@@ -470,7 +475,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, 
       __syncwarp();
       bool bad = false;
       for (int t = lane; t < S; t += 32) {
-        const int32_t x = a.cols[start + t];
+        const int32_t x = ld_nc_hint(a.cols + start + t, stream);
         sm.tile[t] = x;
         bad |= static_cast<uint32_t>(x) >= static_cast<uint32_t>(a.n);
       }
@@ -772,6 +777,8 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
   __shared__ int64_t s_next;  // next batch of walked lists (warps take batches as they finish)
   const int lane = lane_id(), wid = threadIdx.x >> 5;
   unsigned long long acc = 0;
+  bool clean = false;  // the table holds no key and no count (uniform across the block)
+  if (threadIdx.x == 0) s_next = 0;  // reset again after each chunk, behind its last barrier
   const uint32_t qn = HUB ? static_cast<uint32_t>(min64(ws.counters[kCtrItems], ws.items_cap))
                          : ws.counters[kCtrBigQueue];
   for (uint32_t qi = blockIdx.x; qi < qn; qi += gridDim.x) {
@@ -791,13 +798,14 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
     unsigned long long cv = 0;
     for (int64_t c0 = 0; c0 < dv; c0 += H::kCap) {
       const int clen = static_cast<int>(min64(H::kCap, dv - c0));
-      __syncthreads();
-      for (int i = threadIdx.x; i < H::kSlots; i += blockDim.x) {
-        tab[i] = -1;
-        if (MODE == MODE_LOCAL) slot_cnt[i] = 0;
+      __syncthreads();  // the last chunk's clearing and cursor reset are done
+      if (!clean) {  // the first chunk of this block, or after a linear-probing chunk or a bad id
+        for (int i = threadIdx.x; i < H::kSlots; i += blockDim.x) {
+          tab[i] = -1;
+          if (MODE == MODE_LOCAL) slot_cnt[i] = 0;
+        }
+        __syncthreads();
       }
-      if (threadIdx.x == 0) s_next = 0;
-      __syncthreads();
       bool bad = false, homeless = false;
       for (int i = threadIdx.x; i < clen; i += blockDim.x) {
         const int32_t x = a.cols[b + c0 + i];
@@ -805,7 +813,11 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
         else if (!cuckoo_insert<H::kLog2>(tab, x)) homeless = true;
       }
       if (__syncthreads_or(bad)) {
-        if (threadIdx.x == 0) set_err(err, ERR_BAD_ID);
+        if (threadIdx.x == 0) {
+          set_err(err, ERR_BAD_ID);
+          s_next = 0;
+        }
+        clean = false;
         break;
       }
       // a cuckoo build that left a key homeless: rebuild this chunk with linear probing
@@ -819,12 +831,19 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
       // the chunk is a sorted run of the block vertex's list: its ids lie in [lo, hi]
       const int32_t lo = a.cols[b + c0], hi = a.cols[b + c0 + clen - 1];
       for (;;) {
+        // guided batches: a warp takes 32 walked lists while there are many left, then
+        // fewer, so that the warps of the block reach the chunk's end together
         int64_t ub = 0;
-        if (lane == 0) ub = atomicAdd(reinterpret_cast<unsigned long long*>(&s_next),
-                                      static_cast<unsigned long long>(kHashBatch));
+        int size = kHashBatch;
+        if (lane == 0) {
+          const int64_t left = nl - *reinterpret_cast<volatile int64_t*>(&s_next);
+          size = static_cast<int>(max64(kMinHashBatch, min64(kHashBatch, left / (2 * kBlockWarps))));
+          ub = atomicAdd(reinterpret_cast<unsigned long long*>(&s_next), static_cast<unsigned long long>(size));
+        }
         ub = __shfl_sync(FULL, ub, 0);
+        size = __shfl_sync(FULL, size, 0);
         if (ub >= nl) break;
-        const int nb = static_cast<int>(min64(kHashBatch, nl - ub));
+        const int nb = static_cast<int>(min64(size, nl - ub));
         bool act = lane < nb;
         int32_t x = 0;
         int64_t eg = 0;
@@ -849,20 +868,49 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
                                                  dv > H::kCap, c0 == 0, static_cast<int32_t>(dv), linear);
         cv += c;
         if (act && (MODE == MODE_LOCAL || MODE == MODE_LIST_COUNT) && ws.ecount) {
-          // the same lane holds the same edge in every chunk
+          // the first chunk sets the edge's count, later chunks add to it
           if (c0 == 0) ws.ecount[eg] = static_cast<int32_t>(c);
           else ws.ecount[eg] += static_cast<int32_t>(c);
         }
         if (MODE == MODE_LOCAL && c)
           atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + x), static_cast<unsigned long long>(c));
       }
-      if (MODE == MODE_LOCAL) {  // T_w once per (block vertex, w) of this chunk
-        __syncthreads();
-        for (int i = threadIdx.x; i < H::kSlots; i += blockDim.x)
-          if (slot_cnt[i])
-            atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + tab[i]),
-                      static_cast<unsigned long long>(slot_cnt[i]));
+      __syncthreads();  // every probe of this chunk is done
+      if (linear) {  // T_w once per (block vertex, w) of this chunk, over the whole table
+        if (MODE == MODE_LOCAL)
+          for (int i = threadIdx.x; i < H::kSlots; i += blockDim.x)
+            if (slot_cnt[i])
+              atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + tab[i]),
+                        static_cast<unsigned long long>(slot_cnt[i]));
+        clean = false;
+      } else {
+        // cuckoo table: each of the chunk's ids sits in one of its two slots, so its
+        // count is flushed, and then both slots cleared, from the id alone; reading
+        // and clearing are split by a barrier (an id's slot may be another id's partner)
+        if (MODE == MODE_LOCAL) {
+          for (int i = threadIdx.x; i < clen; i += blockDim.x) {
+            const int32_t x = a.cols[b + c0 + i];
+            const int slot = cuckoo_find<H::kLog2>(tab, x);
+            if (slot >= 0 && slot_cnt[slot])
+              atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + x),
+                        static_cast<unsigned long long>(slot_cnt[slot]));
+          }
+          __syncthreads();
+        }
+        for (int i = threadIdx.x; i < clen; i += blockDim.x) {
+          const int32_t x = a.cols[b + c0 + i];
+          const uint32_t h1 = slot_of<H::kLog2>(x), h2 = h1 ^ alt_of<H::kLog2>(x);
+          tab[h1] = -1;
+          tab[h2] = -1;
+          if (MODE == MODE_LOCAL) {
+            slot_cnt[h1] = 0;
+            slot_cnt[h2] = 0;
+          }
+        }
+        clean = true;
       }
+      // every warp has left this chunk's batch loop: the cursor can start over
+      if (threadIdx.x == 0) s_next = 0;
     }
     cv = warp_sum64(cv);
     if (lane == 0) s_red[wid] = cv;

@@ -142,6 +142,8 @@ CountWs carve_count(Carver& c, int32_t n, int64_t m, bool listing);
 
 struct OrientWs {
   int32_t* cursor;      // fill cursor per vertex
+  uint8_t* deg8;        // min(d_v, 255): the order's comparisons gather these bytes (n)
+  uint32_t* fwd;        // bit e: edge e is stored in the list of its first endpoint ((m + 31) / 32 words)
   int32_t* big_queue;   // vertices whose lists the block sorter takes (> kSortWarpCap ids)
   int32_t* mid_queue;   // vertices whose lists the warp sorter takes (33 .. kSortWarpCap ids)
   uint32_t* counters;   // [0] big queue length, [1] mid queue length
@@ -232,5 +234,29 @@ __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 __device__ __forceinline__ void set_err(uint32_t* err, uint32_t bit) { atomicOr(err, bit); }
+
+// L2 eviction priorities as per-instruction cache hints (createpolicy + .L2::cache_hint):
+// they rank this kernel's lines against each other in L2 and change no device setting.
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// Read-only loads with an L2 policy (data that no kernel writes while the reader runs).
+__device__ __forceinline__ int32_t ld_nc_hint(const int32_t* p, uint64_t pol) {
+  int32_t v;
+  asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ int64_t ld_nc_hint(const int64_t* p, uint64_t pol) {
+  int64_t v;
+  asm("ld.global.nc.L2::cache_hint.s64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
+}
 
 }  // namespace tc

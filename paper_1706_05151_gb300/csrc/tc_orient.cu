@@ -10,9 +10,14 @@
 //                   into deg[] (4n bytes, L2-resident for n <= 2^25); the edge
 //                   stream is read evict-first in all three passes (and cols
 //                   written so) to keep deg[] in L2 for the random gathers
-//   k_orient_count  same pass shape, gathers deg[a], deg[b], counts dhat[src]
+//   k_deg8          min(d_v, 255) per vertex (n bytes: L2-resident up to n ~ 2^27)
+//   k_orient_count  same pass shape, gathers the saturated degrees of both
+//                   endpoints (the full ones only when both are >= 255),
+//                   counts dhat[src] and writes one bit per edge: which
+//                   endpoint stores it
 //   exclusive scan  offsets = scan(dhat)
-//   k_scatter       third pass: cols[offsets[src] + cursor[src]++] = dst
+//   k_scatter       third pass, no gathers: the edge's bit gives src;
+//                   cols[offsets[src] + cursor[src]++] = dst
 //   k_sort_small    one thread per vertex: lists of <= 32 ids sorted in
 //                   registers by a bitonic network sized to the warp's longest
 //                   list, the warp's run of lists staged in shared memory;
@@ -26,9 +31,11 @@
 
 namespace tc {
 
-OrientWs carve_orient(Carver& c, int32_t n, int64_t) {
+OrientWs carve_orient(Carver& c, int32_t n, int64_t m) {
   OrientWs w;
   w.cursor = c.take<int32_t>(static_cast<size_t>(n > 0 ? n : 1));
+  w.deg8 = c.take<uint8_t>(static_cast<size_t>(n > 0 ? n : 1));
+  w.fwd = c.take<uint32_t>(static_cast<size_t>(m > 0 ? (m + 31) / 32 : 1));
   w.big_queue = c.take<int32_t>(static_cast<size_t>(n > 0 ? n : 1));
   w.mid_queue = c.take<int32_t>(static_cast<size_t>(n > 0 ? n : 1));
   w.counters = c.take<uint32_t>(4);
@@ -40,11 +47,6 @@ namespace {
 
 __device__ __forceinline__ bool precedes(int64_t da, int32_t a, int64_t db, int32_t b) {
   return da < db || (da == db && a < b);
-}
-
-// Order key of v: its degree (Eq. (1)), or the caller's key (tc_orient_by).
-__device__ __forceinline__ int64_t order_key(const int32_t* deg, const int64_t* keys, int32_t v) {
-  return keys ? keys[v] : static_cast<int64_t>(deg[v]);
 }
 
 __device__ __forceinline__ bool edge_ok(int2 p, int32_t n, uint32_t* err) {
@@ -105,28 +107,55 @@ __device__ __forceinline__ bool edge_valid(int2 p, int32_t n) {
          p.x != p.y;
 }
 
+constexpr int32_t kDeg8Max = 255;
+
+// min(d_v, 255) per vertex: one byte per vertex, so the order's random gathers
+// touch a quarter of the bytes of deg[] (the whole array stays in L2 for n up
+// to about 2^27).
+__global__ void k_deg8(int32_t n, const int32_t* __restrict__ deg, uint8_t* __restrict__ deg8) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride)
+    deg8[v] = static_cast<uint8_t>(min(deg[v], kDeg8Max));
+}
+
+// Eq. (1) from the saturated bytes: they decide the order unless both degrees are
+// at least 255, and then the full degrees are gathered.
+__device__ __forceinline__ bool precedes_deg8(const uint8_t* deg8, const int32_t* deg, int32_t a, int32_t b) {
+  const int32_t sa = __ldg(deg8 + a), sb = __ldg(deg8 + b);
+  if (sa != sb) return sa < sb;
+  if (sa < kDeg8Max) return a < b;
+  return precedes(deg[a], a, deg[b], b);
+}
+
+// Counts dhat and records, one bit per edge, which endpoint stores the edge;
+// k_scatter reads the bits instead of gathering the order's keys again.
 __global__ void k_orient_count(const int2* __restrict__ edges, int64_t m, int32_t n,
-                               const int32_t* __restrict__ deg, const int64_t* __restrict__ keys,
-                               int32_t* __restrict__ dhat) {
+                               const int32_t* __restrict__ deg, const uint8_t* __restrict__ deg8,
+                               const int64_t* __restrict__ keys, int32_t* __restrict__ dhat,
+                               uint32_t* __restrict__ fwd_bits) {
   FOR_EDGES(e, m) {
     const int64_t e = e0 + lane_id();
     int32_t src = 0;
-    bool ok = false;
+    bool ok = false, fwd = false;
     if (e < m) {
       const int2 p = __ldcs(edges + e);
       ok = edge_valid(p, n);
-      if (ok) src = precedes(order_key(deg, keys, p.x), p.x, order_key(deg, keys, p.y), p.y) ? p.x : p.y;
+      if (ok) {
+        fwd = keys ? precedes(keys[p.x], p.x, keys[p.y], p.y) : precedes_deg8(deg8, deg, p.x, p.y);
+        src = fwd ? p.x : p.y;
+      }
     }
+    const unsigned bits = __ballot_sync(FULL, fwd);
+    if (lane_id() == 0 && e0 < m) fwd_bits[e0 >> 5] = bits;
     int hl;
     const int c = run_length(src, ok, &hl);
     if (c) atomicAdd(&dhat[src], c);
   }
 }
 
-__global__ void k_scatter(const int2* __restrict__ edges, int64_t m, int32_t n, const int32_t* __restrict__ deg,
-                          const int64_t* __restrict__ keys, const int64_t* __restrict__ offsets,
-                          int32_t* __restrict__ cursor,
-                          int32_t* __restrict__ cols, uint32_t* err) {
+__global__ void k_scatter(const int2* __restrict__ edges, int64_t m, int32_t n,
+                          const uint32_t* __restrict__ fwd_bits, const int64_t* __restrict__ offsets,
+                          int32_t* __restrict__ cursor, int32_t* __restrict__ cols, uint32_t* err) {
   FOR_EDGES(e, m) {
     const int lane = lane_id();
     const int64_t e = e0 + lane;
@@ -136,7 +165,7 @@ __global__ void k_scatter(const int2* __restrict__ edges, int64_t m, int32_t n, 
       const int2 p = __ldcs(edges + e);
       ok = edge_valid(p, n);
       if (ok) {
-        const bool fwd = precedes(order_key(deg, keys, p.x), p.x, order_key(deg, keys, p.y), p.y);
+        const bool fwd = (__ldg(fwd_bits + (e0 >> 5)) >> lane) & 1u;
         src = fwd ? p.x : p.y;
         dst = fwd ? p.y : p.x;
       }
@@ -396,7 +425,12 @@ cudaError_t launch_orient(Ctx* ctx, int32_t n, int64_t m, const int32_t* edges, 
     }
     {
       Stage st(ctx, s, "orient.orient_count");
-      k_orient_count<<<grid_e, threads, 0, s>>>(ep, m, n, deg, keys, dhat);
+      if (!keys) {
+        const int grid_v = static_cast<int>(min64((n + 255) / 256, static_cast<int64_t>(ctx->sm_count) * 16));
+        k_deg8<<<grid_v, 256, 0, s>>>(n, deg, ws.deg8);
+        counted(ctx);
+      }
+      k_orient_count<<<grid_e, threads, 0, s>>>(ep, m, n, deg, ws.deg8, keys, dhat, ws.fwd);
     }
     counted(ctx, 2);
   }
@@ -407,7 +441,7 @@ cudaError_t launch_orient(Ctx* ctx, int32_t n, int64_t m, const int32_t* edges, 
   }
   if (m > 0) {
     Stage st(ctx, s, "orient.scatter");
-    k_scatter<<<grid_e, threads, 0, s>>>(ep, m, n, deg, keys, offsets, ws.cursor, cols, ctx->d_err);
+    k_scatter<<<grid_e, threads, 0, s>>>(ep, m, n, ws.fwd, offsets, ws.cursor, cols, ctx->d_err);
     counted(ctx);
   }
   if (n > 0) {
