@@ -98,6 +98,25 @@ def test_empty_graphs(tc):
         assert tc.sparsify_count(g, 0.5, 1)[:2] == (0, 0)
 
 
+def test_ids_beyond_one_degree_pass(tc):
+    # about 50M vertex ids with 320k edges: hubs and planted triangles at ids around
+    # 2^24 and 2^25 and at the last id; the oracle's CSR and counts
+    n = 3 * (1 << 24) + 12345
+    rng = np.random.default_rng(41)
+    hubs = np.array([0, (1 << 24) - 1, 1 << 24, (2 << 24) + 7, n - 1], dtype=np.int64)
+    tri = np.concatenate([rng.integers(0, n, (3000, 3)), np.array([[0, 1 << 24, n - 1], [(1 << 24) - 1, 1 << 24,
+                                                                                      (2 << 24) + 7]])])
+    a = np.concatenate([rng.integers(0, n, 300000), np.repeat(hubs, 2000), tri[:, 0], tri[:, 1], tri[:, 0],
+                        np.repeat(hubs, 4)])
+    b = np.concatenate([rng.integers(0, n, 300000), rng.integers(0, n, 10000), tri[:, 1], tri[:, 2], tri[:, 2],
+                        np.tile(hubs, 4)])
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    keep = lo != hi
+    e = np.unique(np.stack([lo[keep], hi[keep]], axis=1), axis=0).astype(np.int32)
+    e = synth.shuffle_edges(e, 42)
+    check_all(tc, n, e)
+
+
 def test_single_triangle_with_isolated_vertices(tc):
     check_all(tc, 10, np.array([[5, 2], [2, 9], [9, 5]], np.int32))
 
