@@ -326,6 +326,40 @@ tc_status tc_partition(tc_ctx* ctx, const tc_graph* g, int32_t parts, int cost, 
 tc_status tc_count_range(tc_ctx* ctx, const tc_graph* g, int32_t v_begin, int32_t v_end, uint64_t* total_dev,
                          int64_t* tv_dev, void* ws, size_t ws_bytes, tc_stream stream);
 
+/*
+ * Counting a graph whose oriented lists stay in HOST memory, for a CSR larger
+ * than the device memory the caller can spare -- the single-GPU form of the
+ * paper's space-efficient algorithm (Section "A Space-efficient Parallel
+ * Algorithm with Non-overlapping Partitioning", its surrogate approach): the
+ * vertices are cut into target ranges whose lists N_u fit half of a device
+ * list buffer; one range at a time is copied in and stays resident while the
+ * apex lists N_v of every vertex stream past it, chunk by chunk, in large
+ * contiguous copies on a second stream (double-buffered, overlapping the
+ * counting), and each chunk counts the triangles (v, u, w) whose middle vertex
+ * u lies in the resident range -- as the surrogate processor of u computes
+ * N_v intersected with N_u for the N_v sent to it.  Every triangle is counted
+ * once (at its apex v and its middle u, Theorem 1), so the sums are exact.
+ *   n, m          graph size; offsets_host int64[n+1], cols_host int32[m]: the
+ *                 oriented CSR in host memory (page-locked for the copies to
+ *                 overlap; pageable memory is copied synchronously)
+ *   total_dev     device uint64[1], overwritten with T
+ *   tv_dev        device int64[n] or NULL: overwritten with T_v
+ *   list_bytes    device bytes for lists inside the workspace: half holds the
+ *                 resident range, a quarter each of two apex chunks; every
+ *                 list must fit a quarter (else TC_ERR_WORKSPACE)
+ *   ws            device workspace of tc_count_streamed_workspace_size(n, m,
+ *                 list_bytes) bytes, 256-byte aligned: the offsets' device
+ *                 copy, the counting kernels' scratch and the list buffer
+ * Host traffic: the whole of cols once per target range plus once more for
+ * the ranges themselves, (ranges + 1) * 4m bytes.  Returns TC_ERR_INVALID_ARG
+ * during a capture.  Stream-ordered like every call; synchronous mode waits
+ * and returns the device checks (TC_ERR_INVALID_GRAPH for a broken CSR).
+ */
+tc_status tc_count_streamed_workspace_size(int32_t n, int64_t m, size_t list_bytes, size_t* bytes);
+tc_status tc_count_streamed(tc_ctx* ctx, int32_t n, int64_t m, const int64_t* offsets_host,
+                            const int32_t* cols_host, uint64_t* total_dev, int64_t* tv_dev, size_t list_bytes,
+                            void* ws, size_t ws_bytes, tc_stream stream);
+
 /* ---- batched form ------------------------------------------------------------ */
 
 /*

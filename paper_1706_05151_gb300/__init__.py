@@ -42,7 +42,7 @@ EXPORTS = ["tc_ctx_create", "tc_ctx_destroy", "tc_ctx_set_async", "tc_ctx_status
            "tc_ctx_set_tuning", "tc_ctx_set_hub_min", "tc_ctx_set_profiling", "tc_ctx_stage_count", "tc_ctx_stage", "tc_ctx_reset_stats", "tc_ctx_launches",
            "tc_count_static", "tc_capture_begin", "tc_capture_end", "tc_exec_launch", "tc_exec_kernels",
            "tc_exec_destroy", "tc_partition", "tc_count_range", "tc_orient_by",
-           "tc_sparsify_count_part"]
+           "tc_sparsify_count_part", "tc_count_streamed_workspace_size", "tc_count_streamed"]
 
 
 class TcError(RuntimeError):
@@ -114,6 +114,8 @@ def load_library(path: str = LIB_PATH):
             "tc_sparsify_count_part": (i32, [vp, G, ctypes.c_double, u64, i32, i32, i32, vp, vp, vp, sz, vp]),
             "tc_partition": (i32, [vp, G, i32, ctypes.c_int, vp, vp, vp, sz, vp]),
             "tc_count_range": (i32, [vp, G, i32, i32, vp, vp, vp, sz, vp]),
+            "tc_count_streamed_workspace_size": (i32, [i32, i64, sz, ctypes.POINTER(sz)]),
+            "tc_count_streamed": (i32, [vp, i32, i64, vp, vp, vp, vp, sz, vp, sz, vp]),
             "tc_capture_begin": (i32, [vp, vp]),
             "tc_capture_end": (i32, [vp, vp, ctypes.POINTER(vp)]),
             "tc_exec_launch": (i32, [vp, vp]),
@@ -413,6 +415,30 @@ def count_range(g: Graph, v_begin: int, v_end: int, total: torch.Tensor, tv: tor
     ws = ctx.workspace(TC_OP_COUNT, g.n, g.m)
     ctx.check(ctx.lib.tc_count_range(ctx.handle, ctypes.byref(g.struct()), int(v_begin), int(v_end), _ptr(total),
                                      _ptr(tv), _ptr(ws), ws.numel(), _stream(ctx.device)))
+
+
+def count_streamed(offsets_host: torch.Tensor, cols_host: torch.Tensor, list_bytes: int, local: bool = False,
+                   ctx: Context | None = None):
+    """tc_count_streamed: T (and T_v if local) of an oriented CSR held in host memory
+    (offsets int64[n+1], cols int32[m]; page-locked for overlapped copies), counted
+    through a device list buffer of list_bytes.  Returns (T, tv or None)."""
+    ctx = ctx or default_context()
+    if offsets_host.is_cuda or cols_host.is_cuda:
+        raise ValueError("count_streamed takes the CSR in host memory")
+    off = offsets_host.contiguous()
+    cols = cols_host.contiguous()
+    assert off.dtype == torch.int64 and cols.dtype == torch.int32
+    n, m = off.numel() - 1, cols.numel()
+    need = sz(0)
+    ctx.check(ctx.lib.tc_count_streamed_workspace_size(n, m, int(list_bytes), ctypes.byref(need)))
+    ws = torch.empty(max(int(need.value), 256), dtype=torch.uint8, device=ctx.device)
+    total = torch.empty(1, dtype=torch.int64, device=ctx.device)
+    tv = torch.empty(max(n, 1), dtype=torch.int64, device=ctx.device) if local else None
+    ctx.check(ctx.lib.tc_count_streamed(ctx.handle, n, m, vp(off.data_ptr()), vp(cols.data_ptr() if m else 0),
+                                        _ptr(total), _ptr(tv), int(list_bytes), _ptr(ws), ws.numel(),
+                                        _stream(ctx.device)))
+    T = int(total.item())
+    return T, (tv[:n] if local else None)
 
 
 @dataclass

@@ -188,6 +188,12 @@ void tc_ctx_destroy(tc_ctx* ctx) {
   cudaSetDevice(ctx->device);
   resolve_stages(ctx);
   for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamDestroy(ctx->copy_stream);
+  }
+  for (cudaEvent_t e : ctx->copy_ev)
+    if (e) cudaEventDestroy(e);
   cudaFree(ctx->d_err);
   cudaFreeHost(ctx->h_err);
   delete ctx;
@@ -341,6 +347,44 @@ tc_status tc_count_range(tc_ctx* ctx, const tc_graph* g, int32_t v_begin, int32_
   a.v_lo = v_begin;
   a.v_hi = v_end;
   return finish(ctx, s, tc::launch_count(ctx, tv_dev ? tc::MODE_LOCAL : tc::MODE_COUNT, a, w, s));
+}
+
+tc_status tc_count_streamed_workspace_size(int32_t n, int64_t m, size_t list_bytes, size_t* bytes) {
+  if (!bytes) return TC_ERR_INVALID_ARG;
+  *bytes = 0;
+  if (n < 0 || m < 0) return TC_ERR_INVALID_ARG;
+  Carver c(nullptr);
+  tc::carve_stream(c, n, m, list_bytes);
+  *bytes = c.size();
+  return TC_OK;
+}
+
+tc_status tc_count_streamed(tc_ctx* ctx, int32_t n, int64_t m, const int64_t* offsets_host, const int32_t* cols_host,
+                            uint64_t* total_dev, int64_t* tv_dev, size_t list_bytes, void* ws, size_t ws_bytes,
+                            tc_stream stream) {
+  if (!ctx) return TC_ERR_INVALID_ARG;
+  if (ctx->capturing) return fail(ctx, TC_ERR_INVALID_ARG, "tc_count_streamed plans its copies on the host: not inside a capture");
+  if (n < 0 || m < 0) return fail(ctx, TC_ERR_INVALID_ARG, "negative n or m");
+  if (!offsets_host || (m > 0 && !cols_host)) return fail(ctx, TC_ERR_INVALID_ARG, "offsets_host or cols_host is NULL");
+  if (!total_dev) return fail(ctx, TC_ERR_INVALID_ARG, "total_dev is NULL");
+  if (!aligned(total_dev, 8) || (tv_dev && !aligned(tv_dev, 8)))
+    return fail(ctx, TC_ERR_INVALID_ARG, "total_dev / tv_dev not 8-byte aligned");
+  size_t need = 0;
+  tc_count_streamed_workspace_size(n, m, list_bytes, &need);
+  if (ws_bytes < need) return fail(ctx, TC_ERR_WORKSPACE, "workspace %zu bytes, need %zu", ws_bytes, need);
+  if (!ws || !aligned(ws, 256)) return fail(ctx, TC_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tc_status st = begin(ctx, s);
+  if (st != TC_OK) return st;
+  Carver c(ws);
+  tc::StreamWs w = tc::carve_stream(c, n, m, list_bytes);
+  const char* why = nullptr;
+  const cudaError_t e = tc::launch_count_streamed(ctx, n, m, offsets_host, cols_host, total_dev, tv_dev, w, s, &why);
+  if (why) {
+    // nothing was copied: the plan was refused on the host
+    return fail(ctx, e == cudaErrorMemoryAllocation ? TC_ERR_WORKSPACE : TC_ERR_INVALID_GRAPH, "%s", why);
+  }
+  return finish(ctx, s, e);
 }
 
 tc_status tc_partition(tc_ctx* ctx, const tc_graph* g, int32_t parts, int cost, int64_t* bounds_dev,

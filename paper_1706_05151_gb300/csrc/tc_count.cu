@@ -92,6 +92,7 @@ __device__ __forceinline__ int32_t list_bounds(const CountArgs& a, int32_t u, in
     set_err(err, ERR_BAD_ID);
     return 0;
   }
+  if (u < a.u_lo || u >= a.u_hi) return 0;  // N_u is not in this call's part of the lists
   // the int32 copy, when there is one, halves the bytes of this random read; it is read
   // about twice per oriented edge, so its lines are the last this kernel lets L2 evict
   const uint64_t keep = l2_policy_evict_last();
@@ -105,7 +106,11 @@ __device__ __forceinline__ int32_t list_bounds(const CountArgs& a, int32_t u, in
     set_err(err, ERR_TOO_LONG);
     return 0;
   }
-  b = lo;
+  if (lo - a.cols_base < 0 || hi - a.cols_base > a.cols_len) {  // outside the array that holds N_u
+    set_err(err, ERR_BAD_CSR);
+    return 0;
+  }
+  b = lo - a.cols_base;
   return static_cast<int32_t>(hi - lo);
 }
 
@@ -437,9 +442,9 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, 
     if (valid) {  // apex offsets and lists are each read once here: first out of L2
       b = ld_nc_hint(a.offsets + v, stream);
       e = ld_nc_hint(a.offsets + v + 1, stream);
-      if (b < 0 || e < b || e > a.m) {
+      if (b < 0 || e < b || e > a.m || b - a.apex_base < 0 || e - a.apex_base > a.apex_len) {
         set_err(err, ERR_BAD_CSR);
-        b = e = 0;
+        b = e = a.apex_base;
       }
     }
     const int64_t d = e - b;
@@ -475,7 +480,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, 
       __syncwarp();
       bool bad = false;
       for (int t = lane; t < S; t += 32) {
-        const int32_t x = ld_nc_hint(a.cols + start + t, stream);
+        const int32_t x = ld_nc_hint(a.apex_cols + (start - a.apex_base) + t, stream);
         sm.tile[t] = x;
         bad |= static_cast<uint32_t>(x) >= static_cast<uint32_t>(a.n);
       }
@@ -792,7 +797,16 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
     } else {
       v = ws.big_queue[qi];
     }
-    const int64_t b = a.offsets[v], e = a.offsets[v + 1];
+    // the hashed list: the apex's own, or on the hub side the hub's N_u
+    const int32_t* hcols = HUB ? a.cols : a.apex_cols;
+    const int64_t hbase = HUB ? a.cols_base : a.apex_base, hlen = HUB ? a.cols_len : a.apex_len;
+    const int64_t b = a.offsets[v];
+    int64_t e = a.offsets[v + 1];
+    if (b - hbase < 0 || e < b || e - hbase > hlen) {  // outside the array that holds it: nothing read
+      if (threadIdx.x == 0) set_err(err, ERR_BAD_CSR);
+      e = b;
+    }
+    const int32_t* hl = hcols + (b - hbase);  // the hashed list's first id
     const int64_t dv = e - b;
     const int64_t nl = HUB ? ent_n : dv;  // lists walked against v's
     unsigned long long cv = 0;
@@ -808,7 +822,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
       }
       bool bad = false, homeless = false;
       for (int i = threadIdx.x; i < clen; i += blockDim.x) {
-        const int32_t x = a.cols[b + c0 + i];
+        const int32_t x = hl[c0 + i];
         if (static_cast<uint32_t>(x) >= static_cast<uint32_t>(a.n)) bad = true;
         else if (!cuckoo_insert<H::kLog2>(tab, x)) homeless = true;
       }
@@ -825,11 +839,11 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
       if (linear) {
         for (int i = threadIdx.x; i < H::kSlots; i += blockDim.x) tab[i] = -1;
         __syncthreads();
-        for (int i = threadIdx.x; i < clen; i += blockDim.x) hash_insert<H::kLog2>(tab, a.cols[b + c0 + i]);
+        for (int i = threadIdx.x; i < clen; i += blockDim.x) hash_insert<H::kLog2>(tab, hl[c0 + i]);
         __syncthreads();
       }
       // the chunk is a sorted run of the block vertex's list: its ids lie in [lo, hi]
-      const int32_t lo = a.cols[b + c0], hi = a.cols[b + c0 + clen - 1];
+      const int32_t lo = hl[c0], hi = hl[c0 + clen - 1];
       for (;;) {
         // guided batches: a warp takes 32 walked lists while there are many left, then
         // fewer, so that the warps of the block reach the chunk's end together
@@ -860,7 +874,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
               act = false;
             }
           } else {
-            x = a.cols[b + ub + lane];
+            x = hl[ub + lane];
             eg = b + ub + lane;
           }
         }
@@ -889,7 +903,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
         // and clearing are split by a barrier (an id's slot may be another id's partner)
         if (MODE == MODE_LOCAL) {
           for (int i = threadIdx.x; i < clen; i += blockDim.x) {
-            const int32_t x = a.cols[b + c0 + i];
+            const int32_t x = hl[c0 + i];
             const int slot = cuckoo_find<H::kLog2>(tab, x);
             if (slot >= 0 && slot_cnt[slot])
               atomicAdd(reinterpret_cast<unsigned long long*>(a.tv + x),
@@ -898,7 +912,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
           __syncthreads();
         }
         for (int i = threadIdx.x; i < clen; i += blockDim.x) {
-          const int32_t x = a.cols[b + c0 + i];
+          const int32_t x = hl[c0 + i];
           const uint32_t h1 = slot_of<H::kLog2>(x), h2 = h1 ^ alt_of<H::kLog2>(x);
           tab[h1] = -1;
           tab[h2] = -1;
@@ -1061,7 +1075,7 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
                                             static_cast<int64_t>(ctx->sm_count) * 8));
   if (hub || a.off32) {
     Stage st(ctx, s, kNames[MODE][2]);
-    if (a.off32) {
+    if (a.off32 && !a.off32_ready) {
       k_off32<<<n_grid, 256, 0, s>>>(a.n, a.m, a.offsets, const_cast<int32_t*>(a.off32));
       counted(ctx);
     }
@@ -1159,14 +1173,30 @@ cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a_in, CountW
   if (a_in.n <= 0) return cudaGetLastError();
   CountArgs a = a_in;
   if (a.v_hi < 0) a.v_hi = a.n;
+  if (a.cols_len < 0) a.cols_len = a.m;
+  if (!a.apex_cols) {
+    a.apex_cols = a.cols;
+    a.apex_base = a.cols_base;
+    a.apex_len = a.cols_len;
+  } else if (a.apex_len < 0) {
+    return cudaErrorInvalidValue;
+  }
+  if (a.u_hi < 0) a.u_hi = a.n;
+  const bool split = a.apex_cols != a.cols || a.apex_base != a.cols_base || a.u_lo > 0 || a.u_hi < a.n;
   if (a.v_lo < 0 || a.v_lo > a.v_hi || a.v_hi > a.n) return cudaErrorInvalidValue;
   // the tile kernel packs a byte address of cols below bit 58 (virtual addresses are far narrower)
-  if ((reinterpret_cast<uintptr_t>(a.cols) + 4u * static_cast<uint64_t>(a.m)) >> 58) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(a.cols) + 4u * static_cast<uint64_t>(a.cols_len)) >> 58) return cudaErrorInvalidValue;
   a.tile_max = (ctx->tile_max > 0 && ctx->tile_max < kTile) ? ctx->tile_max : kTile;
   a.tile_quota = ctx->tile_quota;
   if (ws.off32 && a.m < (int64_t(1) << 31) - 1) a.off32 = ws.off32;  // filled by launch_mode
   // hub side: needs its workspace (absent in the allocation-free entry point)
   a.hub_min = (ws.hub_idx && ctx->hub_min >= 0) ? (ctx->hub_min > 0 ? ctx->hub_min : kHubMinDefault) : 0;
+  // lists in two arrays: the apex-side kernels only (the hub side would hash N_u and
+  // walk apex lists from the wrong array), and no listing
+  if (split) {
+    if (mode == MODE_LIST_COUNT || mode == MODE_LIST_WRITE) return cudaErrorInvalidValue;
+    a.hub_min = 0;
+  }
   switch (mode) {
     case MODE_COUNT: return launch_mode<MODE_COUNT>(ctx, a, ws, s);
     case MODE_LOCAL: return launch_mode<MODE_LOCAL>(ctx, a, ws, s);

@@ -62,6 +62,8 @@ struct Ctx {
   int saved_async = 0;        // async flag before the capture
   int capture_status = 0;     // first failure inside the capture (0 = none)
   Profiler prof;
+  cudaStream_t copy_stream = nullptr;  // tc_count_streamed: host-to-device list copies (created on first use)
+  cudaEvent_t copy_ev[5] = {};         // ... two slots' "copied" and "free" events, one start event
   char last_error[256] = {0};
 };
 
@@ -161,6 +163,19 @@ struct SparsifyWs {
 };
 SparsifyWs carve_sparsify(Carver& c, int32_t n, int64_t m);
 
+// tc_count_streamed: the offsets' device copy, the counting kernels' scratch
+// (no hub side) and the list buffer (half resident range, two quarter slots).
+struct StreamWs {
+  int64_t* offsets;     // n + 1
+  CountWs count;
+  int32_t* lists;       // list_ids
+  int64_t list_ids;
+};
+StreamWs carve_stream(Carver& c, int32_t n, int64_t m, size_t list_bytes);
+cudaError_t launch_count_streamed(Ctx* ctx, int32_t n, int64_t m, const int64_t* offsets_host,
+                                  const int32_t* cols_host, uint64_t* total, int64_t* tv, StreamWs ws,
+                                  cudaStream_t s, const char** why);
+
 struct PartitionWs {
   int64_t* f;           // cost of each vertex (n)
   int64_t* F;           // exclusive scan of f (n + 1)
@@ -211,8 +226,17 @@ struct CountArgs {
   int32_t tile_quota = 0;                     // chunks per warp before its block retires (0: until the work ends)
   const int32_t* off32 = nullptr;             // int32 copy of offsets (set by launch_count when m < 2^31)
   int32_t v_lo = 0, v_hi = -1;                // apex vertices counted: [v_lo, v_hi) (-1: n)
+  bool off32_ready = false;                   // off32 already holds these offsets (a sequence of calls on one graph)
   bool reuse_hub = false;                     // listing write pass: the hub schedule of the counting pass that
                                               // ran just before on the same workspace and thresholds is still valid
+  // Lists held in two places (counting a CSR streamed from host memory): the apex
+  // lists N_v are read at apex_cols[offsets[v] - apex_base] (apex_len ids), the lists
+  // N_u at cols[offsets[u] - cols_base] (cols_len ids), and only edges (v, u) with u in
+  // [u_lo, u_hi) are counted.  Defaults (set by launch_count): one array, every u.
+  const int32_t* apex_cols = nullptr;
+  int64_t apex_base = 0, apex_len = -1;
+  int64_t cols_base = 0, cols_len = -1;
+  int32_t u_lo = 0, u_hi = -1;
 };
 cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a, CountWs ws, cudaStream_t s);
 // Listing: eoff = exclusive scan of ecount (after a MODE_LIST_COUNT or MODE_LOCAL pass).
