@@ -204,14 +204,26 @@ def bench_batched(tc, ctx, dev, args, rank):
     b = tc.make_batch(graphs, dev)
     G, N, E = b.G, b.N, b.E
     stream = torch.cuda.current_stream(dev)
-    # batched: time K calls (cost bin tuned on the union first, outside the timing)
+    # batched: time K calls at the default thresholds and shapes, then tuned on the union
+    # (outside the timing); the per-graph arm below is timed both ways as well
     totals, tv, union = tc.batch(b, True, ctx)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.batch_steps):
+        tc.batch(b, True, ctx)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    batched_default_ms = e0.elapsed_time(e1) / args.batch_steps
     tuned = None
     if not args.no_tune:
         from paper_1706_05151_gb300 import autotune
-        best, times, hub, hub_times = autotune.tune(union, ctx, record=False)
+        shape = {}
+        best, times, hub, hub_times = autotune.tune(union, ctx, record=False, local=True, info=shape)
         tuned = {"tile_max": best, "count_ms_by_tile_max": {str(k): round(v, 3) for k, v in times.items()},
-                 "hub_min": hub, "count_ms_by_hub_min": {str(k): round(v, 3) for k, v in hub_times.items()}}
+                 "hub_min": hub, "count_ms_by_hub_min": {str(k): round(v, 3) for k, v in hub_times.items()},
+                 "tile_shape": shape.get("tile_shape"), "hash_batch": shape.get("hash_batch"),
+                 "count_ms_by_shape": shape.get("shape_ms")}
     del union
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -265,25 +277,38 @@ def bench_batched(tc, ctx, dev, args, rank):
             ctx.check(lib.tc_count_local(ctx.handle, ctypes.byref(gs), ctypes.c_void_p(tp + 8 * g),
                                          ctypes.c_void_p(tvp + 8 * int(vb[g])), None, ctypes.c_void_p(wsp), wsn, hs))
 
-    ctx.set_async(True)
-    ctx.set_tuning(0, 1)  # the plain per-graph form runs with the default thresholds
-    ctx.set_hub_min(0)
-    try:
-        per_graph()  # warm-up
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        per_graph()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ctx.status()
-    finally:
-        ctx.set_async(False)
-    per_graph_ms = e0.elapsed_time(e1)
+    def time_per_graph():
+        ctx.set_async(True)
+        try:
+            per_graph()  # warm-up
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            per_graph()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ctx.status()
+        finally:
+            ctx.set_async(False)
+        return e0.elapsed_time(e1)
+
+    # the per-graph form with the thresholds and shapes tuned on the union (the same as the
+    # batched arm's), then with the defaults
+    per_graph_tuned_ms = time_per_graph()
     same = bool(torch.equal(tot1, totals)) and bool(torch.equal(tv1[:N], tv))
+    ctx.set_tuning(0, 1)
+    ctx.set_hub_min(0)
+    ctx.set_kernel_shape(0, 0, 0)
+    per_graph_ms = time_per_graph()
+    same = same and bool(torch.equal(tot1, totals)) and bool(torch.equal(tv1[:N], tv))
     return {"workload": f"{G} Chung-Lu graphs (gamma 2.1), n log-uniform in [100, 1e5], mean degree U[8, 64]",
             "graphs": G, "vertices": N, "edges": E, "triangles": int(totals.sum().item()),
-            "batched_ms": batched_ms, "per_graph_ms": per_graph_ms, "speedup": per_graph_ms / batched_ms,
-            "captured_ms": captured_ms, "captured_speedup": per_graph_ms / captured_ms,
+            "tuning": "speedup: both arms with the thresholds and shapes tuned on the union; "
+                      "speedup_default: both arms with the library defaults",
+            "batched_ms": batched_ms, "per_graph_ms": per_graph_tuned_ms,
+            "speedup": per_graph_tuned_ms / batched_ms,
+            "batched_default_ms": batched_default_ms, "per_graph_default_ms": per_graph_ms,
+            "speedup_default": per_graph_ms / batched_default_ms,
+            "captured_ms": captured_ms, "captured_speedup": per_graph_tuned_ms / captured_ms,
             "captured_kernels_per_replay": captured_kernels, "captured_results_equal": captured_same,
             "batched_edges_per_s": E / (batched_ms * 1e-3), "results_equal": same, "autotune": tuned}
 
@@ -647,15 +672,19 @@ def measure_workload(args, tc, ctx, dev, name, steps, warmup, e2e_steps, world, 
 
     ctx.set_tuning(0, 1)
     ctx.set_hub_min(0)
+    ctx.set_kernel_shape(0, 0, 0)
     for _ in range(max(warmup, 1)):
         g, T, tv, cc, tri, sp = step()
     tuned = None
     if not args.no_tune:  # pick the cost-bin thresholds on this graph (outside the timed region)
         from paper_1706_05151_gb300 import autotune
         # tuned on the per-vertex pass: with the listing write pass it is most of the step
-        best, times, hub, hub_times = autotune.tune(g, ctx, record=False, local=True)
+        shape = {}
+        best, times, hub, hub_times = autotune.tune(g, ctx, record=False, local=True, info=shape)
         tuned = {"tile_max": best, "local_ms_by_tile_max": {str(k): round(v, 3) for k, v in times.items()},
-                 "hub_min": hub, "local_ms_by_hub_min": {str(k): round(v, 3) for k, v in hub_times.items()}}
+                 "hub_min": hub, "local_ms_by_hub_min": {str(k): round(v, 3) for k, v in hub_times.items()},
+                 "tile_shape": shape.get("tile_shape"), "hash_batch": shape.get("hash_batch"),
+                 "local_ms_by_shape": shape.get("shape_ms")}
         g, T, tv, cc, tri, sp = step()
     W = int((g.deg.to(torch.int64) * g.dhat.to(torch.int64)).sum().item())
     assert int(tv.sum().item()) == 3 * T and len(tri) == T
@@ -817,6 +846,7 @@ def main():
                                          args.also_e2e_steps, world, rank, local_rank, barrier)
     ctx.set_tuning(0, 1)
     ctx.set_hub_min(0)
+    ctx.set_kernel_shape(0, 0, 0)
 
     batched = None
     if args.batch_graphs > 0:

@@ -119,6 +119,17 @@ const char* tc_version(void);
 tc_status tc_ctx_set_tuning(tc_ctx* ctx, int32_t tile_max, int32_t grid_div);
 
 /*
+ * Kernel shapes (no counterpart in the paper; chosen by the autotuner).  The
+ * warp-tile kernel stages tile_ids ids per warp and keeps tile_windows
+ * candidate windows in flight per lane: 256 x 8 (the default, also 0 x 0),
+ * 256 x 4 or 128 x 8 (with 128, apex lists longer than 128 ids go to the block
+ * kernel whatever tile_max says).  hash_batch: walked lists a warp takes at a
+ * time in the block and hub kernels, 32 (default, also 0) or 16.  Other
+ * values: TC_ERR_INVALID_ARG.  Results do not depend on the shapes.
+ */
+tc_status tc_ctx_set_kernel_shape(tc_ctx* ctx, int32_t tile_ids, int32_t tile_windows, int32_t hash_batch);
+
+/*
  * Hub side of the intersection (a cost split; results never depend on it).
  * Theorem 2's work for an oriented edge (v, u) is reading N_v and N_u; the
  * counting kernels keep the apex list N_v on chip and stream N_u.  When N_u

@@ -42,7 +42,8 @@ EXPORTS = ["tc_ctx_create", "tc_ctx_destroy", "tc_ctx_set_async", "tc_ctx_status
            "tc_ctx_set_tuning", "tc_ctx_set_hub_min", "tc_ctx_set_profiling", "tc_ctx_stage_count", "tc_ctx_stage", "tc_ctx_reset_stats", "tc_ctx_launches",
            "tc_count_static", "tc_capture_begin", "tc_capture_end", "tc_exec_launch", "tc_exec_kernels",
            "tc_exec_destroy", "tc_partition", "tc_count_range", "tc_orient_by",
-           "tc_sparsify_count_part", "tc_count_streamed_workspace_size", "tc_count_streamed"]
+           "tc_sparsify_count_part", "tc_count_streamed_workspace_size", "tc_count_streamed",
+           "tc_ctx_set_kernel_shape"]
 
 
 class TcError(RuntimeError):
@@ -134,6 +135,7 @@ def load_library(path: str = LIB_PATH):
             "tc_serve_stats": (i32, [vp, ctypes.POINTER(TcServeStats)]),
             "tc_ctx_set_hub_min": (i32, [vp, i32]),
             "tc_ctx_set_tuning": (i32, [vp, i32, i32]),
+            "tc_ctx_set_kernel_shape": (i32, [vp, i32, i32, i32]),
             "tc_ctx_set_profiling": (i32, [vp, ctypes.c_int]),
             "tc_ctx_stage_count": (ctypes.c_int, [vp]),
             "tc_ctx_stage": (i32, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
@@ -200,6 +202,11 @@ class Context:
     def set_tuning(self, tile_max: int = 0, grid_div: int = 1):
         """tc_ctx_set_tuning: tile/block threshold on |N_v| and the share of the GPU per launch."""
         self.check(self.lib.tc_ctx_set_tuning(self.handle, int(tile_max), int(grid_div)))
+
+    def set_kernel_shape(self, tile_ids: int = 0, tile_windows: int = 0, hash_batch: int = 0):
+        """tc_ctx_set_kernel_shape: tile kernel (256, 8) / (256, 4) / (128, 8); hash batch 32 / 16
+        (zeros: the defaults)."""
+        self.check(self.lib.tc_ctx_set_kernel_shape(self.handle, int(tile_ids), int(tile_windows), int(hash_batch)))
 
     def set_hub_min(self, hub_min: int = 0):
         """tc_ctx_set_hub_min: lists of >= hub_min ids take their longer-list in-edges (0 default, -1 off)."""

@@ -10,11 +10,11 @@
 //
 //   k_count_tile   a warp takes 32 consecutive vertices (one coalesced load of
 //                  their offsets); their lists, contiguous in cols, are staged
-//                  as one shared-memory tile of up to kTile ids (lists longer
+//                  as one shared-memory tile of up to 256 ids (lists longer
 //                  than tile_max are queued for k_count_block).  The tile's
 //                  oriented edges (v, u) are processed 32 at a time.  Short
 //                  lists N_u are laid end to end and walked in 32-wide windows
-//                  (an owner table maps a position to its edge), kTileUnroll
+//                  (an owner table maps a position to its edge), 8 (or 4)
 //                  windows at once so each lane has that many independent
 //                  global loads in flight; long lists are walked one edge at a
 //                  time.  Every candidate w first meets a bitmap filter of the
@@ -47,16 +47,25 @@ namespace tc {
 
 namespace {
 
-constexpr int kTile = 256;           // ids staged per warp; longer lists go to the block kernel
 constexpr int kTileWarps = 4;        // warps per block, tile kernel
-constexpr int kTileBitsLog2 = 13;    // filter bits per tile (1 KB): <= 256 / 8192 false positives
 constexpr int kUnroll = 4;           // candidate windows in flight per lane, block kernel
 constexpr int kShortLen = 32;        // N_u shorter than this is walked end to end with others
 constexpr int kOwnCap = 32 * kShortLen;
-constexpr int kTileUnroll = 8;       // candidate windows in flight per lane, tile kernel
+// Shapes of the tile kernel the autotuner chooses among: ids staged per warp,
+// candidate windows in flight per lane, filter bits (log2) per tile -- 32 bits
+// per staged id, so that at most 1/32 of the candidates pass the filter falsely.
+template <int IDS, int UNROLL, int BITS>
+struct TileShape {
+  static constexpr int kIds = IDS, kUnroll = UNROLL, kBitsLog2 = BITS;
+};
+using TileShapeA = TileShape<256, 8, 13>;  // the default
+using TileShapeB = TileShape<256, 4, 13>;
+using TileShapeC = TileShape<128, 8, 12>;
 constexpr int kBlockWarps = 8;       // warps per block, block kernel
-constexpr int kHashBatch = 32;       // walked lists a warp takes at a time (block and hub kernels, <= 32) ...
-constexpr int kMinHashBatch = 4;     // ... and at least, near the end of a chunk
+// walked lists a warp takes at a time in the block and hub kernels: at most the
+// kernel's BATCH (32 or 16, chosen by the autotuner), at least this many near
+// the end of a chunk
+constexpr int kMinHashBatch = 4;
 constexpr uint64_t kPtrMask = (uint64_t(1) << 58) - 1;  // packed list address: byte address below bit 58
 constexpr uint32_t kSaltMix = 0x7C000000u;              // filter salt (0..31) << 26: bits 58..62 of the packed word
 constexpr int kHubMinDefault = 64;   // default hub_min: lists of at least this many ids take their in-edges
@@ -282,10 +291,10 @@ __device__ __forceinline__ void write_triples(TileWriteBatch& bs, bool has, bool
 // Tile kernel
 // ---------------------------------------------------------------------------
 
-template <int MODE>
+template <int MODE, class SH>
 struct TileSmem {
-  int32_t tile[kTile];
-  uint32_t bits[(1 << kTileBitsLog2) / 32];
+  int32_t tile[SH::kIds];
+  uint32_t bits[(1 << SH::kBitsLog2) / 32];
   int32_t vlo[32];     // tile start of each chunk lane's list (-1 before the group, > S after)
   uint32_t vcnt[32];   // triangles with apex v (chunk lane)
   int32_t qw[64];      // filter survivors: candidate id ...
@@ -294,8 +303,8 @@ struct TileSmem {
 };
 
 // Exact check of the first `cnt` queued survivors, with the per-mode effects.
-template <int MODE>
-__device__ __forceinline__ void exact_flush(TileSmem<MODE>& sm, int cnt, int top, int32_t vbase, const CountArgs& a,
+template <int MODE, class SH>
+__device__ __forceinline__ void exact_flush(TileSmem<MODE, SH>& sm, int cnt, int top, int32_t vbase, const CountArgs& a,
                                             const CountWs& ws, uint32_t* err) {
   auto& bs = sm.bs;
   const int lane = lane_id();
@@ -313,8 +322,8 @@ __device__ __forceinline__ void exact_flush(TileSmem<MODE>& sm, int cnt, int top
 }
 
 // Queue this window's survivors; check 32 of them once 32 are waiting.
-template <int MODE>
-__device__ __forceinline__ void push(TileSmem<MODE>& sm, bool pass, int32_t w, int s, int& qn, int top, int32_t vbase,
+template <int MODE, class SH>
+__device__ __forceinline__ void push(TileSmem<MODE, SH>& sm, bool pass, int32_t w, int s, int& qn, int top, int32_t vbase,
                                      const CountArgs& a, const CountWs& ws, uint32_t* err) {
   const int lane = lane_id();
   const unsigned m = __ballot_sync(FULL, pass);
@@ -326,7 +335,7 @@ __device__ __forceinline__ void push(TileSmem<MODE>& sm, bool pass, int32_t w, i
   }
   qn += __popc(m);
   if (qn >= 32) {
-    exact_flush<MODE>(sm, 32, top, vbase, a, ws, err);
+    exact_flush<MODE, SH>(sm, 32, top, vbase, a, ws, err);
     const int rest = qn - 32;
     int32_t tw = 0, ts = 0;
     if (lane < rest) {
@@ -344,8 +353,8 @@ __device__ __forceinline__ void push(TileSmem<MODE>& sm, bool pass, int32_t w, i
 }
 
 // One batch of the tile's edges; returns the matches of this lane's edge.
-template <int MODE>
-__device__ __forceinline__ uint32_t tile_batch(TileSmem<MODE>& sm, int top, int32_t u, bool act, int64_t eg, int32_t vl,
+template <int MODE, class SH>
+__device__ __forceinline__ uint32_t tile_batch(TileSmem<MODE, SH>& sm, int top, int32_t u, bool act, int64_t eg, int32_t vl,
                                                int32_t lo, int32_t vlen, int32_t vbase, const CountArgs& a,
                                                const CountWs& ws, uint32_t* err) {
   auto& bs = sm.bs;
@@ -356,11 +365,11 @@ __device__ __forceinline__ uint32_t tile_batch(TileSmem<MODE>& sm, int top, int3
   batch_setup(bs, a, ws, u, act, eg, vl, lo, vlen, tot, is_short, len, err, MODE == MODE_LIST_WRITE, 0u,
               vbase + vl, vlen, a.hub_min > 0 ? (a.reuse_hub ? 1 : 2) : 0);
   int qn = 0;
-  for (int32_t p0 = 0; p0 < tot; p0 += 32 * kTileUnroll) {
-    int32_t w[kTileUnroll];
-    uint32_t ss[kTileUnroll];  // edge (bits 0..4) and its filter salt << 26 (bits 26..30)
+  for (int32_t p0 = 0; p0 < tot; p0 += 32 * SH::kUnroll) {
+    int32_t w[SH::kUnroll];
+    uint32_t ss[SH::kUnroll];  // edge (bits 0..4) and its filter salt << 26 (bits 26..30)
 #pragma unroll
-    for (int k = 0; k < kTileUnroll; ++k) {
+    for (int k = 0; k < SH::kUnroll; ++k) {
       const int32_t p = p0 + 32 * k + lane;
       ss[k] = 0;
       w[k] = 0;
@@ -372,10 +381,10 @@ __device__ __forceinline__ uint32_t tile_batch(TileSmem<MODE>& sm, int top, int3
       }
     }
 #pragma unroll
-    for (int k = 0; k < kTileUnroll; ++k) {
+    for (int k = 0; k < SH::kUnroll; ++k) {
       const int32_t p = p0 + 32 * k + lane;
-      const bool pass = p < tot && ftest<kTileBitsLog2>(sm.bits, w[k], ss[k] & kSaltMix);
-      push<MODE>(sm, pass, w[k], static_cast<int>(ss[k] & 31u), qn, top, vbase, a, ws, err);
+      const bool pass = p < tot && ftest<SH::kBitsLog2>(sm.bits, w[k], ss[k] & kSaltMix);
+      push<MODE, SH>(sm, pass, w[k], static_cast<int>(ss[k] & 31u), qn, top, vbase, a, ws, err);
     }
   }
   unsigned lm = __ballot_sync(FULL, len > 0 && !is_short);
@@ -385,22 +394,22 @@ __device__ __forceinline__ uint32_t tile_batch(TileSmem<MODE>& sm, int top, int3
     const int32_t* lb = reinterpret_cast<const int32_t*>(bs.pk[e] & kPtrMask);  // N_u
     const int32_t le = __shfl_sync(FULL, len, e);
     const uint32_t se = static_cast<uint32_t>(bs.salt[e]) << 26;
-    for (int32_t p0 = 0; p0 < le; p0 += 32 * kTileUnroll) {
-      int32_t w[kTileUnroll];
+    for (int32_t p0 = 0; p0 < le; p0 += 32 * SH::kUnroll) {
+      int32_t w[SH::kUnroll];
 #pragma unroll
-      for (int k = 0; k < kTileUnroll; ++k) {
+      for (int k = 0; k < SH::kUnroll; ++k) {
         const int32_t p = p0 + 32 * k + lane;
         w[k] = p < le ? __ldca(lb + p) : 0;
       }
 #pragma unroll
-      for (int k = 0; k < kTileUnroll; ++k) {
+      for (int k = 0; k < SH::kUnroll; ++k) {
         const int32_t p = p0 + 32 * k + lane;
-        const bool pass = p < le && ftest<kTileBitsLog2>(sm.bits, w[k], se);
-        push<MODE>(sm, pass, w[k], e, qn, top, vbase, a, ws, err);
+        const bool pass = p < le && ftest<SH::kBitsLog2>(sm.bits, w[k], se);
+        push<MODE, SH>(sm, pass, w[k], e, qn, top, vbase, a, ws, err);
       }
     }
   }
-  if (qn) exact_flush<MODE>(sm, qn, top, vbase, a, ws, err);
+  if (qn) exact_flush<MODE, SH>(sm, qn, top, vbase, a, ws, err);
   __syncwarp();
   return act ? bs.cnt[lane] : 0u;
 }
@@ -422,12 +431,12 @@ __device__ __forceinline__ void add_graph_totals(const CountArgs& a, bool in_gro
   if (head && in_group && sum) atomicAdd(a.graph_total + key, static_cast<unsigned long long>(sum));
 }
 
-template <int MODE>
+template <int MODE, class SH>
 __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, CountWs ws, uint32_t* err) {
-  __shared__ TileSmem<MODE> s_t[kTileWarps];
+  __shared__ TileSmem<MODE, SH> s_t[kTileWarps];
   __shared__ unsigned long long s_sum[kTileWarps];
   const int lane = lane_id(), wid = threadIdx.x >> 5;
-  TileSmem<MODE>& sm = s_t[wid];
+  TileSmem<MODE, SH>& sm = s_t[wid];
   unsigned long long acc = 0;
   const uint64_t stream = l2_policy_evict_first();
   for (int32_t chunk = 0; a.tile_quota <= 0 || chunk < a.tile_quota; ++chunk) {
@@ -459,13 +468,13 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, 
       if (big) ws.big_queue[qb + __popc(bigmask & lanemask_lt())] = v;
     }
     // Groups: maximal runs of consecutive short lists whose ids fit one tile.
-    // live: lanes whose list this kernel counts (a live list has <= tile_max <= kTile ids, so it opens a group)
+    // live: lanes whose list this kernel counts (a live list has <= tile_max <= SH::kIds ids, so it opens a group)
     const unsigned live = __ballot_sync(FULL, valid && !big && !skip);
     int g0 = live ? __ffs(live) - 1 : 32;
     while (g0 < 32) {
       const int32_t len = (lane >= g0 && valid && !big && !skip) ? static_cast<int32_t>(d) : 0;
       const int32_t incl = warp_incl_scan(len);
-      const bool stop = lane >= g0 && (!valid || big || skip || incl > kTile);
+      const bool stop = lane >= g0 && (!valid || big || skip || incl > SH::kIds);
       const unsigned smask = __ballot_sync(FULL, stop);
       const int g1 = smask ? __ffs(smask) - 1 : 32;
       if (g1 == g0) {  // lane g0 is past the end, a queued long list or skipped: go to the next live lane
@@ -484,7 +493,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, 
         sm.tile[t] = x;
         bad |= static_cast<uint32_t>(x) >= static_cast<uint32_t>(a.n);
       }
-      for (int i = lane; i < (1 << kTileBitsLog2) / 32; i += 32) sm.bits[i] = 0u;
+      for (int i = lane; i < (1 << SH::kBitsLog2) / 32; i += 32) sm.bits[i] = 0u;
       const int32_t lo = incl - len;
       sm.vlo[lane] = lane < g0 ? -1 : (lane < g1 ? lo : S + 1);
       sm.vcnt[lane] = 0;
@@ -494,7 +503,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, 
         continue;
       }
       __syncwarp();
-      for (int i = 0; i < glen; ++i) fset<kTileBitsLog2>(sm.bits, sm.tile[lo + i], static_cast<uint32_t>(lane) << 26);
+      for (int i = 0; i < glen; ++i) fset<SH::kBitsLog2>(sm.bits, sm.tile[lo + i], static_cast<uint32_t>(lane) << 26);
       const int maxlen = __reduce_max_sync(FULL, glen);
       const int top = maxlen > 0 ? 1 << (31 - __clz(maxlen)) : 0;
       __syncwarp();
@@ -504,7 +513,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, 
         const int vl = act ? search32(sm.vlo, static_cast<int32_t>(t)) : 0;
         const int32_t u = act ? sm.tile[t] : 0;
         const int32_t vlen = __shfl_sync(FULL, glen, vl);
-        const uint32_t c = tile_batch<MODE>(sm, top, u, act, start + t, vl, sm.vlo[vl], vlen,
+        const uint32_t c = tile_batch<MODE, SH>(sm, top, u, act, start + t, vl, sm.vlo[vl], vlen,
                                             static_cast<int32_t>(base), a, ws, err);
         if (act && (MODE == MODE_LOCAL || MODE == MODE_LIST_COUNT) && ws.ecount)
           __stcs(ws.ecount + start + t, static_cast<int32_t>(c));  // write-once stream: evict-first
@@ -772,7 +781,7 @@ __device__ __forceinline__ uint32_t hash_batch(HashBatch& bs, const int32_t* tab
 // edges (x, u) recorded for u's side); N_u is hashed and each N_x walked.
 // Both: the block vertex's list is hashed in chunks of H::kCap ids; the
 // lane's vertex gets its edge's matches, the block vertex their sum.
-template <int MODE, bool HUB>
+template <int MODE, bool HUB, int BATCH>
 __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a, CountWs ws, uint32_t* err) {
   using H = HashCfg<MODE>;
   extern __shared__ int32_t tab[];
@@ -848,10 +857,10 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
         // guided batches: a warp takes 32 walked lists while there are many left, then
         // fewer, so that the warps of the block reach the chunk's end together
         int64_t ub = 0;
-        int size = kHashBatch;
+        int size = BATCH;
         if (lane == 0) {
           const int64_t left = nl - *reinterpret_cast<volatile int64_t*>(&s_next);
-          size = static_cast<int>(max64(kMinHashBatch, min64(kHashBatch, left / (2 * kBlockWarps))));
+          size = static_cast<int>(max64(kMinHashBatch, min64(BATCH, left / (2 * kBlockWarps))));
           ub = atomicAdd(reinterpret_cast<unsigned long long*>(&s_next), static_cast<unsigned long long>(size));
         }
         ub = __shfl_sync(FULL, ub, 0);
@@ -1050,16 +1059,50 @@ __global__ void k_clustering(int32_t n, const int32_t* __restrict__ deg, const i
   }
 }
 
-// Dynamic shared memory of k_count_block<MODE, HUB> beyond the 48 KB default: opt in once per device.
-template <int MODE, bool HUB>
+// Dynamic shared memory of k_count_block<MODE, HUB, BATCH> beyond the 48 KB default: opt in once per device.
+template <int MODE, bool HUB, int BATCH>
 cudaError_t block_smem_optin(Ctx* ctx, size_t smem) {
   static bool attr_set[64] = {false};
   if (ctx->device >= 0 && ctx->device < 64 && !attr_set[ctx->device]) {
-    const cudaError_t e = cudaFuncSetAttribute(k_count_block<MODE, HUB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const cudaError_t e = cudaFuncSetAttribute(k_count_block<MODE, HUB, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     attr_set[ctx->device] = true;
   }
+  return cudaSuccess;
+}
+
+// The tile kernel of shape SH: persistent grid, but no more blocks than there is work
+// for (small graphs leave room for other streams); with a chunk quota, enough blocks
+// that every chunk is taken although each warp stops after its quota.
+template <int MODE, class SH>
+cudaError_t launch_tile(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s, const char* name) {
+  const int64_t chunks = (static_cast<int64_t>(a.v_hi) - a.v_lo + 31) / 32;
+  const int tgrid = a.tile_quota > 0
+      ? static_cast<int>(max64(1, (chunks + static_cast<int64_t>(kTileWarps) * a.tile_quota - 1) /
+                                      (static_cast<int64_t>(kTileWarps) * a.tile_quota)))
+      : static_cast<int>(min64(
+            persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_tile<MODE, SH>), kTileWarps * 32, 0),
+            max64(1, (chunks + kTileWarps - 1) / kTileWarps)));
+  Stage st(ctx, s, name);
+  k_count_tile<MODE, SH><<<tgrid, kTileWarps * 32, 0, s>>>(a, ws, ctx->d_err);
+  counted(ctx);
+  return cudaSuccess;
+}
+
+// The block kernel (apex side) or the hub kernel, taking BATCH walked lists at a time.
+template <int MODE, bool HUB, int BATCH>
+cudaError_t launch_hash(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s, const char* name) {
+  const size_t smem = HashCfg<MODE>::kBytes;
+  cudaError_t e = block_smem_optin<MODE, HUB, BATCH>(ctx, smem);
+  if (e != cudaSuccess) return e;
+  int grid = persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_block<MODE, HUB, BATCH>),
+                               kBlockWarps * 32, smem);
+  // the apex side gets at most m / (tile_max + 1) lists
+  if (!HUB) grid = static_cast<int>(min64(grid, max64(1, a.m / (a.tile_max + 1))));
+  Stage st(ctx, s, name);
+  k_count_block<MODE, HUB, BATCH><<<grid, kBlockWarps * 32, smem, s>>>(a, ws, ctx->d_err);
+  counted(ctx);
   return cudaSuccess;
 }
 
@@ -1084,30 +1127,17 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
       counted(ctx);
     }
   }
-  // persistent grids, but no more blocks than there is work for (small graphs leave room for other streams)
-  // (with a chunk quota, enough blocks that every chunk is taken although each warp stops after its quota)
-  const int64_t chunks = (static_cast<int64_t>(a.v_hi) - a.v_lo + 31) / 32;
-  const int tgrid = a.tile_quota > 0
-      ? static_cast<int>(max64(1, (chunks + static_cast<int64_t>(kTileWarps) * a.tile_quota - 1) /
-                                      (static_cast<int64_t>(kTileWarps) * a.tile_quota)))
-      : static_cast<int>(min64(
-            persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_tile<MODE>), kTileWarps * 32, 0),
-            max64(1, (chunks + kTileWarps - 1) / kTileWarps)));
-  {
-    Stage st(ctx, s, kNames[MODE][0]);
-    k_count_tile<MODE><<<tgrid, kTileWarps * 32, 0, s>>>(a, ws, ctx->d_err);
+  cudaError_t e;
+  switch (ctx->tile_shape) {
+    case 1: e = launch_tile<MODE, TileShapeB>(ctx, a, ws, s, kNames[MODE][0]); break;
+    case 2: e = launch_tile<MODE, TileShapeC>(ctx, a, ws, s, kNames[MODE][0]); break;
+    default: e = launch_tile<MODE, TileShapeA>(ctx, a, ws, s, kNames[MODE][0]); break;
   }
-  const size_t smem = HashCfg<MODE>::kBytes;
-  cudaError_t e = block_smem_optin<MODE, false>(ctx, smem);
   if (e != cudaSuccess) return e;
-  const int bgrid = static_cast<int>(min64(
-      persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_block<MODE, false>), kBlockWarps * 32, smem),
-      max64(1, a.m / (a.tile_max + 1))));  // at most m / (tile_max + 1) lists go to this kernel
-  {
-    Stage st(ctx, s, kNames[MODE][1]);
-    k_count_block<MODE, false><<<bgrid, kBlockWarps * 32, smem, s>>>(a, ws, ctx->d_err);
-  }
-  counted(ctx, 2);
+  const bool b16 = ctx->hash_batch == 16;
+  e = b16 ? launch_hash<MODE, false, 16>(ctx, a, ws, s, kNames[MODE][1])
+          : launch_hash<MODE, false, 32>(ctx, a, ws, s, kNames[MODE][1]);
+  if (e != cudaSuccess) return e;
   if (hub) {
     if (!a.reuse_hub) {
       Stage st(ctx, s, kNames[MODE][2]);
@@ -1120,12 +1150,9 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
       k_hub_items<<<n_grid, 256, 0, s>>>(ws);
       counted(ctx, a.n > 0 ? 5 : 3);
     }
-    if ((e = block_smem_optin<MODE, true>(ctx, smem)) != cudaSuccess) return e;
-    const int hgrid = persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_block<MODE, true>),
-                                        kBlockWarps * 32, smem);
-    Stage st(ctx, s, kNames[MODE][3]);
-    k_count_block<MODE, true><<<hgrid, kBlockWarps * 32, smem, s>>>(a, ws, ctx->d_err);
-    counted(ctx);
+    e = b16 ? launch_hash<MODE, true, 16>(ctx, a, ws, s, kNames[MODE][3])
+            : launch_hash<MODE, true, 32>(ctx, a, ws, s, kNames[MODE][3]);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
@@ -1186,7 +1213,8 @@ cudaError_t launch_count(Ctx* ctx, CountMode mode, const CountArgs& a_in, CountW
   if (a.v_lo < 0 || a.v_lo > a.v_hi || a.v_hi > a.n) return cudaErrorInvalidValue;
   // the tile kernel packs a byte address of cols below bit 58 (virtual addresses are far narrower)
   if ((reinterpret_cast<uintptr_t>(a.cols) + 4u * static_cast<uint64_t>(a.cols_len)) >> 58) return cudaErrorInvalidValue;
-  a.tile_max = (ctx->tile_max > 0 && ctx->tile_max < kTile) ? ctx->tile_max : kTile;
+  const int tile_ids = ctx->tile_shape == 2 ? TileShapeC::kIds : TileShapeA::kIds;
+  a.tile_max = (ctx->tile_max > 0 && ctx->tile_max < tile_ids) ? ctx->tile_max : tile_ids;
   a.tile_quota = ctx->tile_quota;
   if (ws.off32 && a.m < (int64_t(1) << 31) - 1) a.off32 = ws.off32;  // filled by launch_mode
   // hub side: needs its workspace (absent in the allocation-free entry point)

@@ -58,6 +58,8 @@ struct Ctx {
   int32_t grid_div = 1;       // tuning: persistent grids use 1/grid_div of the resident capacity
   int32_t hub_min = 0;        // tuning: hub side for |N_u| >= hub_min (0: default, -1: off)
   int32_t tile_quota = 0;     // vertex chunks per warp before a tile-kernel block retires (0: persistent)
+  int32_t tile_shape = 0;     // tuning: tile kernel shape (0: 256 ids x 8 windows, 1: 256 x 4, 2: 128 x 8)
+  int32_t hash_batch = 32;    // tuning: walked lists per warp batch in the block and hub kernels (32 or 16)
   int capturing = 0;          // inside tc_capture_begin .. tc_capture_end
   int saved_async = 0;        // async flag before the capture
   int capture_status = 0;     // first failure inside the capture (0 = none)

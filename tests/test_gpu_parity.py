@@ -329,6 +329,44 @@ def test_results_independent_of_tuning(tc, make):
         ctx.set_tuning(0, 1)
 
 
+@pytest.mark.parametrize("make", [
+    lambda: (1 << 14, synth.rmat(14, 16, 43)),
+    lambda: (900, synth.complete(900)),          # every apex list in the block kernel, in chunks
+    lambda: (1 << 15, synth.ba(1 << 15, 16, 44)),
+])
+def test_results_independent_of_kernel_shape(tc, make):
+    # every instantiation of the tile kernel (ids x windows) and of the hash kernels (batch),
+    # with the hub side on and off: identical T, T_v and triangle list
+    n, e = make()
+    ctx = tc.default_context()
+    g = tc.orient(to_dev(e), n)
+    ref = oracle.count(n, e, local=True, listing=True)
+    r = ref["tri"]
+    ref_rows = r[np.lexsort((r[:, 2], r[:, 1], r[:, 0]))]
+    try:
+        for (ids, windows) in ((256, 8), (256, 4), (128, 8)):
+            for hb in (32, 16):
+                for hub in (0, -1):
+                    ctx.set_kernel_shape(ids, windows, hb)
+                    ctx.set_hub_min(hub)
+                    T, tv, cc, tri = tc.analyze(g)
+                    assert T == ref["T"] and np.array_equal(tv.cpu().numpy(), ref["tv"]), (ids, windows, hb, hub)
+                    t = tri.cpu().numpy()
+                    assert np.array_equal(t[np.lexsort((t[:, 2], t[:, 1], t[:, 0]))], ref_rows)
+                    assert tc.count(g) == T
+    finally:
+        ctx.set_kernel_shape(0, 0, 0)
+        ctx.set_hub_min(0)
+
+
+def test_kernel_shape_refuses_unknown_shapes(tc):
+    ctx = tc.default_context()
+    for bad in ((512, 8, 32), (256, 2, 32), (256, 8, 8), (128, 4, 0)):
+        with pytest.raises(tc.TcError):
+            ctx.set_kernel_shape(*bad)
+    ctx.set_kernel_shape(0, 0, 0)
+
+
 def test_autotuner_records_a_candidate(tc, tmp_path):
     from paper_1706_05151_gb300 import autotune
     n = 1 << 13
@@ -344,6 +382,7 @@ def test_autotuner_records_a_candidate(tc, tmp_path):
     finally:
         tc.default_context().set_tuning(0, 1)
         tc.default_context().set_hub_min(0)
+        tc.default_context().set_kernel_shape(0, 0, 0)
 
 
 def test_listing_of_lists_longer_than_one_hash_chunk(tc):
