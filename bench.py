@@ -83,7 +83,7 @@ def recorded_traffic(kernel: str, workload: str):
     except Exception:
         return None
     for r in rec.get("records", []):
-        if r.get("kernel") == kernel and r.get("workload") == workload and \
+        if r.get("kernel") == kernel and r.get("workload") == workload and r.get("covers_pass") and \
                 r.get("source_sha") == source_sha(*r.get("sources", [])):
             return float(r["dram_bytes_per_launch"])
     return None
