@@ -177,7 +177,8 @@ tc_status tc_workspace_size(tc_op op, int32_t n, int64_t m, size_t* bytes);
  * self-loops and repeated edges give TC_ERR_INVALID_GRAPH (outputs are then
  * unspecified but every access stays in bounds).  Lists longer than 2^24 ids
  * give TC_ERR_UNSUPPORTED (the degree order bounds |N_v| by sqrt(2m); lists
- * beyond 32768 ids, possible under other orders, are sorted in global memory).
+ * beyond 32768 ids are sorted in global memory; under the degree order a list
+ * holds at most about sqrt(2m) ids, which passes 32768 once m exceeds ~5.4e8).
  */
 tc_status tc_orient(tc_ctx* ctx, int32_t n, int64_t m, const int32_t* edges, int64_t* offsets,
                     int32_t* cols, int32_t* deg, int32_t* dhat, void* ws, size_t ws_bytes,

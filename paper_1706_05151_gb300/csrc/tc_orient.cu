@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(1024) k_sort_big(const int64_t* __restrict__ o
     const int32_t v = big_queue[qi];
     const int64_t beg = offsets[v];
     const int64_t len = offsets[v + 1] - beg;
-    if (len > kSortBlockCap) {  // only under other orders (tc_orient_by): sort in place in global memory
+    if (len > kSortBlockCap) {  // longer than shared memory holds (any order): sort in place in global memory
       if (len > kMaxListLen) {
         if (threadIdx.x == 0) set_err(err, ERR_TOO_LONG);
         continue;

@@ -262,6 +262,18 @@ void finish_request(tc_server* s, Request& r, tc_status st) {
   s->cv_done.notify_all();
 }
 
+// A launch that failed part way: kernels already queued on the slot's stream may
+// still run, and the slot's completion callback may still be queued.  Wait for the
+// stream before the workspace and result go back to the pool and the slot is reused.
+void fail_launched(tc_server* s, Request& r) {
+  if (r.slot >= 0 && static_cast<size_t>(r.slot) < s->slots.size()) {
+    Slot& sl = *s->slots[static_cast<size_t>(r.slot)];
+    cudaStreamSynchronize(sl.stream);
+    sl.done.store(false);
+  }
+  finish_request(s, r, TC_ERR_CUDA);
+}
+
 tc_status status_of(uint32_t bits) {
   if (!bits) return TC_OK;
   if (bits & tc::ERR_CAPACITY) return TC_ERR_CAPACITY;
@@ -308,7 +320,7 @@ void worker_loop(tc_server* s) {
           r.t_wait = Clock::now();
           continue;
         }
-        if (launch_request(s, r, g) != cudaSuccess) finish_request(s, r, TC_ERR_CUDA);
+        if (launch_request(s, r, g) != cudaSuccess) fail_launched(s, r);
         continue;
       }
       if (r.kind != TC_REQ_LIST) r.T = *sl.h_total;
@@ -324,7 +336,7 @@ void worker_loop(tc_server* s) {
       if (r.tri) {
         r.state = REQ_RUNNING;
         progressed = true;
-        if (launch_request(s, r, s->graphs[r.graph]) != cudaSuccess) finish_request(s, r, TC_ERR_CUDA);
+        if (launch_request(s, r, s->graphs[r.graph]) != cudaSuccess) fail_launched(s, r);
       } else {
         const size_t need = 12 * static_cast<size_t>(r.T > 0 ? r.T : 1);
         const bool never = need + s->resident_bytes > s->pool.capacity();
@@ -379,7 +391,7 @@ void worker_loop(tc_server* s) {
       s->slots[static_cast<size_t>(free_slot)]->ticket = r.ticket;
       s->admitted++;
       it = s->pending.erase(it);
-      if (launch_request(s, r, g) != cudaSuccess) finish_request(s, r, TC_ERR_CUDA);
+      if (launch_request(s, r, g) != cudaSuccess) fail_launched(s, r);
     }
     lk.unlock();
     if (!progressed) {  // sleep until a completion or submission (or a timeout check is due)
