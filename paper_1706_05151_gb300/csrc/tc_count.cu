@@ -365,6 +365,8 @@ __device__ __forceinline__ uint32_t tile_batch(TileSmem<MODE, SH>& sm, int top, 
   batch_setup(bs, a, ws, u, act, eg, vl, lo, vlen, tot, is_short, len, err, MODE == MODE_LIST_WRITE, 0u,
               vbase + vl, vlen, a.hub_min > 0 ? (a.reuse_hub ? 1 : 2) : 0);
   int qn = 0;
+  // candidate lists are read evict-first: a list is read again only after many others,
+  // and the lines it would keep are better spent on the list bounds (read evict-last)
   for (int32_t p0 = 0; p0 < tot; p0 += 32 * SH::kUnroll) {
     int32_t w[SH::kUnroll];
     uint32_t ss[SH::kUnroll];  // edge (bits 0..4) and its filter salt << 26 (bits 26..30)
@@ -376,7 +378,7 @@ __device__ __forceinline__ uint32_t tile_batch(TileSmem<MODE, SH>& sm, int top, 
       if (p < tot) {
         const int s = bs.own[p];
         const uint64_t pk = bs.pk[s];
-        w[k] = __ldca(reinterpret_cast<const int32_t*>(pk & kPtrMask) + p);
+        w[k] = ld_nc_hint(reinterpret_cast<const int32_t*>(pk & kPtrMask) + p, l2_policy_evict_first());
         ss[k] = static_cast<uint32_t>(s) | (static_cast<uint32_t>(pk >> 32) & kSaltMix);
       }
     }
@@ -399,7 +401,7 @@ __device__ __forceinline__ uint32_t tile_batch(TileSmem<MODE, SH>& sm, int top, 
 #pragma unroll
       for (int k = 0; k < SH::kUnroll; ++k) {
         const int32_t p = p0 + 32 * k + lane;
-        w[k] = p < le ? __ldca(lb + p) : 0;
+        w[k] = p < le ? ld_nc_hint(lb + p, l2_policy_evict_first()) : 0;
       }
 #pragma unroll
       for (int k = 0; k < SH::kUnroll; ++k) {

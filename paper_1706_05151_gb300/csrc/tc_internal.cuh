@@ -279,6 +279,11 @@ __device__ __forceinline__ int32_t ld_nc_hint(const int32_t* p, uint64_t pol) {
   asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
   return v;
 }
+__device__ __forceinline__ int32_t ld_nc_l1na_hint(const int32_t* p, uint64_t pol) {  // and no L1 allocation
+  int32_t v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
 __device__ __forceinline__ int64_t ld_nc_hint(const int64_t* p, uint64_t pol) {
   int64_t v;
   asm("ld.global.nc.L2::cache_hint.s64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
