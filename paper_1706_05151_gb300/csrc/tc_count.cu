@@ -876,9 +876,15 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
           if (HUB) {  // edge (x, v): v sits at position en.y of N_x
             const int2 en = ws.hub_ent[ent_lo + ub + lane];
             x = en.x;
-            if (static_cast<uint32_t>(x) < static_cast<uint32_t>(a.n) && en.y >= 0 &&
-                a.offsets[x] + en.y < a.offsets[x + 1]) {
-              eg = a.offsets[x] + en.y;
+            // N_x's bounds from the int32 offsets when there are some: the same line
+            // serves list_bounds right after (the hub side never splits the lists)
+            int64_t xb = 0, xe = 0;
+            if (static_cast<uint32_t>(x) < static_cast<uint32_t>(a.n)) {
+              xb = a.off32 ? a.off32[x] : a.offsets[x];
+              xe = a.off32 ? a.off32[x + 1] : a.offsets[x + 1];
+            }
+            if (static_cast<uint32_t>(x) < static_cast<uint32_t>(a.n) && en.y >= 0 && xb + en.y < xe) {
+              eg = xb + en.y;
             } else {  // an entry the fill pass did not write: skip it, report the mismatch
               set_err(err, ERR_BAD_CSR);
               x = 0;
