@@ -117,6 +117,20 @@ def test_ids_beyond_one_degree_pass(tc):
     check_all(tc, n, e)
 
 
+@pytest.mark.parametrize("make", [
+    lambda: (1 << 20, synth.ba(1 << 20, 16, 45)),
+    lambda: ((1 << 20) + 777, synth.er((1 << 20) + 777, 6_000_000, 46)),   # a ragged last bucket
+    lambda: (1 << 20, synth.shuffle_edges(synth.rmat(20, 16, 47), 48)),    # any edge order and direction
+])
+def test_orientation_at_a_million_vertices(tc, make):
+    # n >= 2^20 with mean degree >= 8, a ragged vertex count, and a shuffled edge order
+    from oracle import par
+    n, e = make()
+    adj, g = check_orient(tc, n, e)
+    off, cols, _ = adj.orient()
+    assert tc.count(g) == par.count(n, off, cols, local=False)["T"]
+
+
 def test_single_triangle_with_isolated_vertices(tc):
     check_all(tc, 10, np.array([[5, 2], [2, 9], [9, 5]], np.int32))
 
