@@ -355,8 +355,12 @@ def test_results_independent_of_kernel_shape(tc, make):
     ctx = tc.default_context()
     g = tc.orient(to_dev(e), n)
     ref = oracle.count(n, e, local=True, listing=True)
-    r = ref["tri"]
-    ref_rows = r[np.lexsort((r[:, 2], r[:, 1], r[:, 0]))]
+
+    def row_keys(t: torch.Tensor) -> torch.Tensor:
+        # each triple as one int64 (n < 2^21), sorted on the device: equal iff the row sets are
+        t = t.to(torch.int64)
+        return torch.sort((t[:, 0] * n + t[:, 1]) * n + t[:, 2]).values
+    ref_keys = row_keys(torch.from_numpy(ref["tri"]).cuda())
     try:
         for (ids, windows) in ((256, 8), (256, 4), (128, 8)):
             for hb in (32, 16):
@@ -365,8 +369,7 @@ def test_results_independent_of_kernel_shape(tc, make):
                     ctx.set_hub_min(hub)
                     T, tv, cc, tri = tc.analyze(g)
                     assert T == ref["T"] and np.array_equal(tv.cpu().numpy(), ref["tv"]), (ids, windows, hb, hub)
-                    t = tri.cpu().numpy()
-                    assert np.array_equal(t[np.lexsort((t[:, 2], t[:, 1], t[:, 0]))], ref_rows)
+                    assert torch.equal(row_keys(tri), ref_keys)
                     assert tc.count(g) == T
     finally:
         ctx.set_kernel_shape(0, 0, 0)
