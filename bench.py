@@ -222,7 +222,7 @@ def bench_batched(tc, ctx, dev, args, rank):
         best, times, hub, hub_times = autotune.tune(union, ctx, record=False, local=True, info=shape)
         tuned = {"tile_max": best, "count_ms_by_tile_max": {str(k): round(v, 3) for k, v in times.items()},
                  "hub_min": hub, "count_ms_by_hub_min": {str(k): round(v, 3) for k, v in hub_times.items()},
-                 "tile_shape": shape.get("tile_shape"), "hash_batch": shape.get("hash_batch"),
+                 "tile_shape": shape.get("tile_shape"), "hash_shape": shape.get("hash_shape"),
                  "count_ms_by_shape": shape.get("shape_ms")}
     del union
     torch.cuda.synchronize(dev)
@@ -297,7 +297,7 @@ def bench_batched(tc, ctx, dev, args, rank):
     same = bool(torch.equal(tot1, totals)) and bool(torch.equal(tv1[:N], tv))
     ctx.set_tuning(0, 1)
     ctx.set_hub_min(0)
-    ctx.set_kernel_shape(0, 0, 0)
+    ctx.set_kernel_shape(0, 0, 0, 0)
     per_graph_ms = time_per_graph()
     same = same and bool(torch.equal(tot1, totals)) and bool(torch.equal(tv1[:N], tv))
     return {"workload": f"{G} Chung-Lu graphs (gamma 2.1), n log-uniform in [100, 1e5], mean degree U[8, 64]",
@@ -672,7 +672,7 @@ def measure_workload(args, tc, ctx, dev, name, steps, warmup, e2e_steps, world, 
 
     ctx.set_tuning(0, 1)
     ctx.set_hub_min(0)
-    ctx.set_kernel_shape(0, 0, 0)
+    ctx.set_kernel_shape(0, 0, 0, 0)
     for _ in range(max(warmup, 1)):
         g, T, tv, cc, tri, sp = step()
     tuned = None
@@ -683,7 +683,7 @@ def measure_workload(args, tc, ctx, dev, name, steps, warmup, e2e_steps, world, 
         best, times, hub, hub_times = autotune.tune(g, ctx, record=False, local=True, info=shape)
         tuned = {"tile_max": best, "local_ms_by_tile_max": {str(k): round(v, 3) for k, v in times.items()},
                  "hub_min": hub, "local_ms_by_hub_min": {str(k): round(v, 3) for k, v in hub_times.items()},
-                 "tile_shape": shape.get("tile_shape"), "hash_batch": shape.get("hash_batch"),
+                 "tile_shape": shape.get("tile_shape"), "hash_shape": shape.get("hash_shape"),
                  "local_ms_by_shape": shape.get("shape_ms")}
         g, T, tv, cc, tri, sp = step()
     W = int((g.deg.to(torch.int64) * g.dhat.to(torch.int64)).sum().item())
@@ -846,7 +846,7 @@ def main():
                                          args.also_e2e_steps, world, rank, local_rank, barrier)
     ctx.set_tuning(0, 1)
     ctx.set_hub_min(0)
-    ctx.set_kernel_shape(0, 0, 0)
+    ctx.set_kernel_shape(0, 0, 0, 0)
 
     batched = None
     if args.batch_graphs > 0:

@@ -124,10 +124,13 @@ tc_status tc_ctx_set_tuning(tc_ctx* ctx, int32_t tile_max, int32_t grid_div);
  * candidate windows in flight per lane: 256 x 8 (the default, also 0 x 0),
  * 256 x 4 or 128 x 8 (with 128, apex lists longer than 128 ids go to the block
  * kernel whatever tile_max says).  hash_batch: walked lists a warp takes at a
- * time in the block and hub kernels, 32 (default, also 0) or 16.  Other
- * values: TC_ERR_INVALID_ARG.  Results do not depend on the shapes.
+ * time in the block and hub kernels, 32 (default, also 0) or 16; hash_windows:
+ * candidate windows each lane of those kernels keeps in flight, 4 (default,
+ * also 0) or 8.  Other values: TC_ERR_INVALID_ARG.  Results do not depend on
+ * the shapes.
  */
-tc_status tc_ctx_set_kernel_shape(tc_ctx* ctx, int32_t tile_ids, int32_t tile_windows, int32_t hash_batch);
+tc_status tc_ctx_set_kernel_shape(tc_ctx* ctx, int32_t tile_ids, int32_t tile_windows, int32_t hash_batch,
+                                  int32_t hash_windows);
 
 /*
  * Hub side of the intersection (a cost split; results never depend on it).

@@ -135,7 +135,7 @@ def load_library(path: str = LIB_PATH):
             "tc_serve_stats": (i32, [vp, ctypes.POINTER(TcServeStats)]),
             "tc_ctx_set_hub_min": (i32, [vp, i32]),
             "tc_ctx_set_tuning": (i32, [vp, i32, i32]),
-            "tc_ctx_set_kernel_shape": (i32, [vp, i32, i32, i32]),
+            "tc_ctx_set_kernel_shape": (i32, [vp, i32, i32, i32, i32]),
             "tc_ctx_set_profiling": (i32, [vp, ctypes.c_int]),
             "tc_ctx_stage_count": (ctypes.c_int, [vp]),
             "tc_ctx_stage": (i32, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
@@ -203,10 +203,11 @@ class Context:
         """tc_ctx_set_tuning: tile/block threshold on |N_v| and the share of the GPU per launch."""
         self.check(self.lib.tc_ctx_set_tuning(self.handle, int(tile_max), int(grid_div)))
 
-    def set_kernel_shape(self, tile_ids: int = 0, tile_windows: int = 0, hash_batch: int = 0):
-        """tc_ctx_set_kernel_shape: tile kernel (256, 8) / (256, 4) / (128, 8); hash batch 32 / 16
-        (zeros: the defaults)."""
-        self.check(self.lib.tc_ctx_set_kernel_shape(self.handle, int(tile_ids), int(tile_windows), int(hash_batch)))
+    def set_kernel_shape(self, tile_ids: int = 0, tile_windows: int = 0, hash_batch: int = 0, hash_windows: int = 0):
+        """tc_ctx_set_kernel_shape: tile kernel (256, 8) / (256, 4) / (128, 8); hash kernels' batch
+        32 / 16 and windows in flight 4 / 8 (zeros: the defaults)."""
+        self.check(self.lib.tc_ctx_set_kernel_shape(self.handle, int(tile_ids), int(tile_windows), int(hash_batch),
+                                                    int(hash_windows)))
 
     def set_hub_min(self, hub_min: int = 0):
         """tc_ctx_set_hub_min: lists of >= hub_min ids take their longer-list in-edges (0 default, -1 off)."""

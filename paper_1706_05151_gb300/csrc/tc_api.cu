@@ -230,7 +230,8 @@ tc_status tc_ctx_set_tuning(tc_ctx* ctx, int32_t tile_max, int32_t grid_div) {
   return TC_OK;
 }
 
-tc_status tc_ctx_set_kernel_shape(tc_ctx* ctx, int32_t tile_ids, int32_t tile_windows, int32_t hash_batch) {
+tc_status tc_ctx_set_kernel_shape(tc_ctx* ctx, int32_t tile_ids, int32_t tile_windows, int32_t hash_batch,
+                                  int32_t hash_windows) {
   if (!ctx) return TC_ERR_INVALID_ARG;
   int shape = -1;
   if ((tile_ids == 0 && tile_windows == 0) || (tile_ids == 256 && tile_windows == 8)) shape = 0;
@@ -239,8 +240,11 @@ tc_status tc_ctx_set_kernel_shape(tc_ctx* ctx, int32_t tile_ids, int32_t tile_wi
   if (shape < 0) return fail(ctx, TC_ERR_INVALID_ARG, "tile shape must be 256x8, 256x4 or 128x8");
   if (hash_batch != 0 && hash_batch != 16 && hash_batch != 32)
     return fail(ctx, TC_ERR_INVALID_ARG, "hash batch must be 16 or 32");
+  if (hash_windows != 0 && hash_windows != 4 && hash_windows != 8)
+    return fail(ctx, TC_ERR_INVALID_ARG, "hash windows must be 4 or 8");
   ctx->tile_shape = shape;
   ctx->hash_batch = hash_batch ? hash_batch : 32;
+  ctx->hash_windows = hash_windows ? hash_windows : 4;
   return TC_OK;
 }
 

@@ -48,7 +48,6 @@ namespace tc {
 namespace {
 
 constexpr int kTileWarps = 4;        // warps per block, tile kernel
-constexpr int kUnroll = 4;           // candidate windows in flight per lane, block kernel
 constexpr int kShortLen = 32;        // N_u shorter than this is walked end to end with others
 constexpr int kOwnCap = 32 * kShortLen;
 // Shapes of the tile kernel the autotuner chooses among: ids staged per warp,
@@ -707,7 +706,7 @@ __device__ __forceinline__ void emit_long(bool f, int32_t w, int32_t u_e, int32_
 // vertex v's list: block kernel, edges (v, u) with u on this lane if `act`,
 // walking N_u; hub kernel (HUB), edges (x, v) with x on this lane, walking N_x.
 // eg is the lane's edge (its position in cols).  Returns the lane's matches.
-template <int MODE, bool HUB>
+template <int MODE, bool HUB, int UNROLL>
 __device__ __forceinline__ uint32_t hash_batch(HashBatch& bs, const int32_t* tab, uint32_t* slot_cnt, int32_t lo,
                                                int32_t hi, int32_t u, bool act, int64_t eg, int32_t v,
                                                const CountArgs& a, const CountWs& ws, uint32_t* err,
@@ -728,11 +727,11 @@ __device__ __forceinline__ uint32_t hash_batch(HashBatch& bs, const int32_t* tab
   // write pass: this lane's edge's output cursor (0 for edges without triangles: they have no lanes)
   int64_t wbase = (kWrite && act && len > 0) ? ws.eoff[eg] + erun0 : 0;
   const int32_t slen = is_short ? len : 0;
-  for (int32_t p0 = 0; p0 < tot; p0 += 32 * kUnroll) {
-    int32_t w[kUnroll];
-    int s[kUnroll];
+  for (int32_t p0 = 0; p0 < tot; p0 += 32 * UNROLL) {
+    int32_t w[UNROLL];
+    int s[UNROLL];
 #pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
+    for (int k = 0; k < UNROLL; ++k) {
       const int32_t p = p0 + 32 * k + lane;
       s[k] = 0;
       w[k] = -1;
@@ -742,7 +741,7 @@ __device__ __forceinline__ uint32_t hash_batch(HashBatch& bs, const int32_t* tab
       }
     }
 #pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
+    for (int k = 0; k < UNROLL; ++k) {
       const int slot = (w[k] >= lo && w[k] <= hi) ? table_find<L>(tab, w[k], linear) : -1;
       if (kWrite) emit_short<HUB>(slot >= 0, s[k], w[k], p0 + 32 * k, excl, slen, u, v, wbase, a, err);
       else hash_record<MODE>(bs, slot_cnt, slot, s[k]);
@@ -756,15 +755,15 @@ __device__ __forceinline__ uint32_t hash_batch(HashBatch& bs, const int32_t* tab
     const int32_t le = __shfl_sync(FULL, len, e);
     const int32_t u_e = __shfl_sync(FULL, u, e);
     int64_t base_e = __shfl_sync(FULL, wbase, e);
-    for (int32_t p0 = 0; p0 < le; p0 += 32 * kUnroll) {
-      int32_t w[kUnroll];
+    for (int32_t p0 = 0; p0 < le; p0 += 32 * UNROLL) {
+      int32_t w[UNROLL];
 #pragma unroll
-      for (int k = 0; k < kUnroll; ++k) {
+      for (int k = 0; k < UNROLL; ++k) {
         const int32_t p = p0 + 32 * k + lane;
         w[k] = p < le ? a.cols[b + p] : -1;
       }
 #pragma unroll
-      for (int k = 0; k < kUnroll; ++k) {
+      for (int k = 0; k < UNROLL; ++k) {
         const int slot = (w[k] >= lo && w[k] <= hi) ? table_find<L>(tab, w[k], linear) : -1;
         if (kWrite) emit_long<HUB>(slot >= 0, w[k], u_e, v, base_e, a, err);
         else hash_record<MODE>(bs, slot_cnt, slot, e);
@@ -783,7 +782,7 @@ __device__ __forceinline__ uint32_t hash_batch(HashBatch& bs, const int32_t* tab
 // edges (x, u) recorded for u's side); N_u is hashed and each N_x walked.
 // Both: the block vertex's list is hashed in chunks of H::kCap ids; the
 // lane's vertex gets its edge's matches, the block vertex their sum.
-template <int MODE, bool HUB, int BATCH>
+template <int MODE, bool HUB, int BATCH, int UNROLL>
 __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a, CountWs ws, uint32_t* err) {
   using H = HashCfg<MODE>;
   extern __shared__ int32_t tab[];
@@ -895,7 +894,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, 4) k_count_block(CountArgs a
             eg = b + ub + lane;
           }
         }
-        const uint32_t c = hash_batch<MODE, HUB>(s_b[wid], tab, slot_cnt, lo, hi, x, act, eg, v, a, ws, err,
+        const uint32_t c = hash_batch<MODE, HUB, UNROLL>(s_b[wid], tab, slot_cnt, lo, hi, x, act, eg, v, a, ws, err,
                                                  dv > H::kCap, c0 == 0, static_cast<int32_t>(dv), linear);
         cv += c;
         if (act && (MODE == MODE_LOCAL || MODE == MODE_LIST_COUNT) && ws.ecount) {
@@ -1067,12 +1066,12 @@ __global__ void k_clustering(int32_t n, const int32_t* __restrict__ deg, const i
   }
 }
 
-// Dynamic shared memory of k_count_block<MODE, HUB, BATCH> beyond the 48 KB default: opt in once per device.
-template <int MODE, bool HUB, int BATCH>
+// Dynamic shared memory of k_count_block<MODE, HUB, BATCH, UNROLL> beyond the 48 KB default: opt in once per device.
+template <int MODE, bool HUB, int BATCH, int UNROLL>
 cudaError_t block_smem_optin(Ctx* ctx, size_t smem) {
   static bool attr_set[64] = {false};
   if (ctx->device >= 0 && ctx->device < 64 && !attr_set[ctx->device]) {
-    const cudaError_t e = cudaFuncSetAttribute(k_count_block<MODE, HUB, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const cudaError_t e = cudaFuncSetAttribute(k_count_block<MODE, HUB, BATCH, UNROLL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     attr_set[ctx->device] = true;
@@ -1098,20 +1097,30 @@ cudaError_t launch_tile(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
   return cudaSuccess;
 }
 
-// The block kernel (apex side) or the hub kernel, taking BATCH walked lists at a time.
-template <int MODE, bool HUB, int BATCH>
+// The block kernel (apex side) or the hub kernel, taking BATCH walked lists at a time
+// with UNROLL candidate windows in flight per lane.
+template <int MODE, bool HUB, int BATCH, int UNROLL>
 cudaError_t launch_hash(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s, const char* name) {
   const size_t smem = HashCfg<MODE>::kBytes;
-  cudaError_t e = block_smem_optin<MODE, HUB, BATCH>(ctx, smem);
+  cudaError_t e = block_smem_optin<MODE, HUB, BATCH, UNROLL>(ctx, smem);
   if (e != cudaSuccess) return e;
-  int grid = persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_block<MODE, HUB, BATCH>),
+  int grid = persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_block<MODE, HUB, BATCH, UNROLL>),
                                kBlockWarps * 32, smem);
   // the apex side gets at most m / (tile_max + 1) lists
   if (!HUB) grid = static_cast<int>(min64(grid, max64(1, a.m / (a.tile_max + 1))));
   Stage st(ctx, s, name);
-  k_count_block<MODE, HUB, BATCH><<<grid, kBlockWarps * 32, smem, s>>>(a, ws, ctx->d_err);
+  k_count_block<MODE, HUB, BATCH, UNROLL><<<grid, kBlockWarps * 32, smem, s>>>(a, ws, ctx->d_err);
   counted(ctx);
   return cudaSuccess;
+}
+
+// The hash kernels' shape: lists per warp batch (32 or 16), windows in flight (4 or 8).
+template <int MODE, bool HUB>
+cudaError_t launch_hash_shape(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s, const char* name) {
+  const bool w8 = ctx->hash_windows == 8;
+  if (ctx->hash_batch == 16) return w8 ? launch_hash<MODE, HUB, 16, 8>(ctx, a, ws, s, name)
+                                       : launch_hash<MODE, HUB, 16, 4>(ctx, a, ws, s, name);
+  return w8 ? launch_hash<MODE, HUB, 32, 8>(ctx, a, ws, s, name) : launch_hash<MODE, HUB, 32, 4>(ctx, a, ws, s, name);
 }
 
 template <int MODE>
@@ -1142,9 +1151,7 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
     default: e = launch_tile<MODE, TileShapeA>(ctx, a, ws, s, kNames[MODE][0]); break;
   }
   if (e != cudaSuccess) return e;
-  const bool b16 = ctx->hash_batch == 16;
-  e = b16 ? launch_hash<MODE, false, 16>(ctx, a, ws, s, kNames[MODE][1])
-          : launch_hash<MODE, false, 32>(ctx, a, ws, s, kNames[MODE][1]);
+  e = launch_hash_shape<MODE, false>(ctx, a, ws, s, kNames[MODE][1]);
   if (e != cudaSuccess) return e;
   if (hub) {
     if (!a.reuse_hub) {
@@ -1158,8 +1165,7 @@ cudaError_t launch_mode(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
       k_hub_items<<<n_grid, 256, 0, s>>>(ws);
       counted(ctx, a.n > 0 ? 5 : 3);
     }
-    e = b16 ? launch_hash<MODE, true, 16>(ctx, a, ws, s, kNames[MODE][3])
-            : launch_hash<MODE, true, 32>(ctx, a, ws, s, kNames[MODE][3]);
+    e = launch_hash_shape<MODE, true>(ctx, a, ws, s, kNames[MODE][3]);
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();

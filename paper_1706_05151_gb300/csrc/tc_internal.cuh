@@ -60,6 +60,7 @@ struct Ctx {
   int32_t tile_quota = 0;     // vertex chunks per warp before a tile-kernel block retires (0: persistent)
   int32_t tile_shape = 0;     // tuning: tile kernel shape (0: 256 ids x 8 windows, 1: 256 x 4, 2: 128 x 8)
   int32_t hash_batch = 32;    // tuning: walked lists per warp batch in the block and hub kernels (32 or 16)
+  int32_t hash_windows = 4;   // tuning: candidate windows in flight per lane in those kernels (4 or 8)
   int capturing = 0;          // inside tc_capture_begin .. tc_capture_end
   int saved_async = 0;        // async flag before the capture
   int capture_status = 0;     // first failure inside the capture (0 = none)

@@ -24,8 +24,8 @@ class FakeCtx:
     def set_hub_min(self, hub_min):
         self.calls.append(("hub_min", hub_min))
 
-    def set_kernel_shape(self, tile_ids, windows, hash_batch):
-        self.calls.append(("shape", tile_ids, windows, hash_batch))
+    def set_kernel_shape(self, tile_ids, windows, hash_batch, hash_windows):
+        self.calls.append(("shape", tile_ids, windows, hash_batch, hash_windows))
 
 
 def fake_graph(n, m, dmax):
@@ -51,7 +51,8 @@ def test_tune_picks_fastest_then_tunes_hub_at_it_and_records(tmp_path, monkeypat
     def fake_time(tc, g, ctx, tile_max, repeats, hub_min=0, local=False, shape=None):
         seen.append((tile_max, hub_min, local, shape))
         if shape is not None:
-            return {((256, 4), 32): 2.4, ((128, 8), 32): 2.6, ((256, 4), 16): 2.45}[shape]
+            return {((256, 4), (32, 4)): 2.4, ((128, 8), (32, 4)): 2.6, ((256, 4), (16, 4)): 2.45,
+                    ((256, 4), (32, 8)): 2.3}[shape]
         return tile_ms[tile_max] if hub_min == 0 else hub_ms[hub_min]
 
     monkeypatch.setattr(autotune, "time_count", fake_time)
@@ -64,20 +65,21 @@ def test_tune_picks_fastest_then_tunes_hub_at_it_and_records(tmp_path, monkeypat
     # hub_min candidates are all timed at the winning tile_max, on the per-vertex pass
     assert [s[:3] for s in seen if s[1] != 0 and s[3] is None] == \
         [(128, h, True) for h in autotune.HUB_CANDIDATES if h != 0]
-    # then the other tile shapes at both winners, then hash batch 16 at the best tile shape
-    assert [s for s in seen if s[3] is not None] == [(128, 64, True, ((256, 4), 32)), (128, 64, True, ((128, 8), 32)),
-                                                     (128, 64, True, ((256, 4), 16))]
-    assert info["tile_shape"] == [256, 4] and info["hash_batch"] == 32
-    assert info["shape_ms"] == {"tile256x8": 2.5, "tile256x4": 2.4, "tile128x8": 2.6, "batch32": 2.4,
-                                "batch16": 2.45}
-    assert ctx.calls[-3:] == [("tile_max", 128, 1), ("hub_min", 64), ("shape", 256, 4, 32)]
+    # then the other tile shapes at both winners, then the other hash-kernel shapes at the best tile shape
+    assert [s for s in seen if s[3] is not None] == [
+        (128, 64, True, ((256, 4), (32, 4))), (128, 64, True, ((128, 8), (32, 4))),
+        (128, 64, True, ((256, 4), (16, 4))), (128, 64, True, ((256, 4), (32, 8)))]
+    assert info["tile_shape"] == [256, 4] and info["hash_shape"] == [32, 8]
+    assert info["shape_ms"] == {"tile256x8": 2.5, "tile256x4": 2.4, "tile128x8": 2.6, "hash32x4": 2.4,
+                                "hash16x4": 2.45, "hash32x8": 2.3}
+    assert ctx.calls[-3:] == [("tile_max", 128, 1), ("hub_min", 64), ("shape", 256, 4, 32, 8)]
     rec = json.load(open(path))[autotune.shape_class(g)]
     assert rec["tile_max"] == 128 and rec["hub_min"] == 64 and rec["n"] == 4096 and rec["m"] == 65536
-    assert rec["tile_shape"] == [256, 4] and rec["hash_batch"] == 32
+    assert rec["tile_shape"] == [256, 4] and rec["hash_shape"] == [32, 8]
     # a later run on a graph of the same shape class starts from the recorded choices
     ctx2 = FakeCtx()
     assert autotune.apply(fake_graph(4000, 64000, 600), ctx=ctx2, path=path) == (128, 64)
-    assert ctx2.calls == [("tile_max", 128, 1), ("hub_min", 64), ("shape", 256, 4, 32)]
+    assert ctx2.calls == [("tile_max", 128, 1), ("hub_min", 64), ("shape", 256, 4, 32, 8)]
     # another shape class falls back to the defaults (0 = the library's own)
     assert autotune.apply(fake_graph(4096, 65536, 5000), ctx=FakeCtx(), path=path) == (0, 0)
 

@@ -35,7 +35,7 @@ def run():
     yield tc, e, g, T, tv, cc, tri
     tc.default_context().set_tuning(0, 1)
     tc.default_context().set_hub_min(0)
-    tc.default_context().set_kernel_shape(0, 0, 0)
+    tc.default_context().set_kernel_shape(0, 0, 0, 0)
     tc.default_context().release_workspace()
     del g, tv, cc, tri
     torch.cuda.empty_cache()

@@ -349,7 +349,7 @@ def test_results_independent_of_tuning(tc, make):
     lambda: (1 << 15, synth.ba(1 << 15, 16, 44)),
 ])
 def test_results_independent_of_kernel_shape(tc, make):
-    # every instantiation of the tile kernel (ids x windows) and of the hash kernels (batch),
+    # every instantiation of the tile kernel (ids x windows) and of the hash kernels (batch x windows),
     # with the hub side on and off: identical T, T_v and triangle list
     n, e = make()
     ctx = tc.default_context()
@@ -363,25 +363,25 @@ def test_results_independent_of_kernel_shape(tc, make):
     ref_keys = row_keys(torch.from_numpy(ref["tri"]).cuda())
     try:
         for (ids, windows) in ((256, 8), (256, 4), (128, 8)):
-            for hb in (32, 16):
+            for hb, hw in ((32, 4), (16, 4), (32, 8), (16, 8)):
                 for hub in (0, -1):
-                    ctx.set_kernel_shape(ids, windows, hb)
+                    ctx.set_kernel_shape(ids, windows, hb, hw)
                     ctx.set_hub_min(hub)
                     T, tv, cc, tri = tc.analyze(g)
-                    assert T == ref["T"] and np.array_equal(tv.cpu().numpy(), ref["tv"]), (ids, windows, hb, hub)
+                    assert T == ref["T"] and np.array_equal(tv.cpu().numpy(), ref["tv"]), (ids, windows, hb, hw, hub)
                     assert torch.equal(row_keys(tri), ref_keys)
                     assert tc.count(g) == T
     finally:
-        ctx.set_kernel_shape(0, 0, 0)
+        ctx.set_kernel_shape(0, 0, 0, 0)
         ctx.set_hub_min(0)
 
 
 def test_kernel_shape_refuses_unknown_shapes(tc):
     ctx = tc.default_context()
-    for bad in ((512, 8, 32), (256, 2, 32), (256, 8, 8), (128, 4, 0)):
+    for bad in ((512, 8, 32, 4), (256, 2, 32, 4), (256, 8, 8, 4), (128, 4, 0, 0), (256, 8, 32, 6)):
         with pytest.raises(tc.TcError):
             ctx.set_kernel_shape(*bad)
-    ctx.set_kernel_shape(0, 0, 0)
+    ctx.set_kernel_shape(0, 0, 0, 0)
 
 
 def test_autotuner_records_a_candidate(tc, tmp_path):
@@ -399,7 +399,7 @@ def test_autotuner_records_a_candidate(tc, tmp_path):
     finally:
         tc.default_context().set_tuning(0, 1)
         tc.default_context().set_hub_min(0)
-        tc.default_context().set_kernel_shape(0, 0, 0)
+        tc.default_context().set_kernel_shape(0, 0, 0, 0)
 
 
 def test_listing_of_lists_longer_than_one_hash_chunk(tc):
