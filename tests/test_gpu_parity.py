@@ -131,6 +131,30 @@ def test_orientation_at_a_million_vertices(tc, make):
     assert tc.count(g) == par.count(n, off, cols, local=False)["T"]
 
 
+def _top_and_bottom_ids(n, seed):
+    # 60k random edges among the first and the last 40k ids, plus triangles across them
+    rng = np.random.default_rng(seed)
+    ids = np.concatenate([np.arange(40000), np.arange(n - 40000, n)])
+    a, b = ids[rng.integers(0, len(ids), 60000)], ids[rng.integers(0, len(ids), 60000)]
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    keep = lo != hi
+    return synth.shuffle_edges(np.unique(np.stack([lo[keep], hi[keep]], axis=1), axis=0).astype(np.int32), seed)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: (1 << 27, _top_and_bottom_ids(1 << 27, 67)),
+    lambda: ((1 << 27) + 1, _top_and_bottom_ids((1 << 27) + 1, 68)),
+    lambda: ((1 << 23) + 5, synth.shuffle_edges(synth.er((1 << 23) + 5, 2_000_000, 70), 71)),
+])
+def test_orientation_over_large_id_ranges(tc, make):
+    # sparse graphs whose ids span up to 2^27 + 1 vertices: the whole CSR, d_v and dhat_v, and T
+    n, e = make()
+    adj, g = check_orient(tc, n, e)
+    assert tc.count(g) == adj.count()["T"]
+    del g
+    torch.cuda.empty_cache()
+
+
 def test_single_triangle_with_isolated_vertices(tc):
     check_all(tc, 10, np.array([[5, 2], [2, 9], [9, 5]], np.int32))
 
