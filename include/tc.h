@@ -201,6 +201,23 @@ tc_status tc_orient_by(tc_ctx* ctx, int32_t n, int64_t m, const int32_t* edges, 
                        int64_t* offsets, int32_t* cols, int32_t* deg, int32_t* dhat, void* ws, size_t ws_bytes,
                        tc_stream stream);
 
+/*
+ * tc_orient from an edge list in host memory (the same orientation; the
+ * upload overlap has no counterpart in the paper).  edges_host: page-locked
+ * host int32[m][2] (cudaHostAlloc or cudaHostRegister; other host memory gives
+ * TC_ERR_INVALID_ARG); it must stay valid until the stream has passed this
+ * call.  edges_dev: device int32[m][2], 8-byte aligned, caller-owned, which
+ * receives the copy (overwritten; afterwards it holds the edge list).  The list
+ * is copied in chunks of 2^24 edges on a stream of the context's own, and the
+ * degree pass counts each chunk as soon as it has landed, so the copy and the
+ * degree pass overlap; the rest of the orientation runs after the last chunk.
+ * The copies start only after the work queued on `stream` before this call.
+ * Outputs, workspace (TC_OP_ORIENT) and errors as tc_orient.
+ */
+tc_status tc_orient_host(tc_ctx* ctx, int32_t n, int64_t m, const int32_t* edges_host, int32_t* edges_dev,
+                         int64_t* offsets, int32_t* cols, int32_t* deg, int32_t* dhat, void* ws, size_t ws_bytes,
+                         tc_stream stream);
+
 /* ---- counting (Figure 2 counting loop; Theorems 1-2) --------------------- */
 
 /*

@@ -43,7 +43,7 @@ EXPORTS = ["tc_ctx_create", "tc_ctx_destroy", "tc_ctx_set_async", "tc_ctx_status
            "tc_count_static", "tc_capture_begin", "tc_capture_end", "tc_exec_launch", "tc_exec_kernels",
            "tc_exec_destroy", "tc_partition", "tc_count_range", "tc_orient_by",
            "tc_sparsify_count_part", "tc_count_streamed_workspace_size", "tc_count_streamed",
-           "tc_ctx_set_kernel_shape"]
+           "tc_ctx_set_kernel_shape", "tc_orient_host"]
 
 
 class TcError(RuntimeError):
@@ -112,6 +112,7 @@ def load_library(path: str = LIB_PATH):
             "tc_analyze": (i32, [vp, G, vp, vp, vp, vp, i64, ctypes.POINTER(i64), vp, sz, vp]),
             "tc_batch": (i32, [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
             "tc_orient_by": (i32, [vp, i32, i64, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+            "tc_orient_host": (i32, [vp, i32, i64, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
             "tc_sparsify_count_part": (i32, [vp, G, ctypes.c_double, u64, i32, i32, i32, vp, vp, vp, sz, vp]),
             "tc_partition": (i32, [vp, G, i32, ctypes.c_int, vp, vp, vp, sz, vp]),
             "tc_count_range": (i32, [vp, G, i32, i32, vp, vp, vp, sz, vp]),
@@ -300,6 +301,35 @@ def orient(edges: torch.Tensor, n: int, ctx: Context | None = None, keys: torch.
         ctx.check(ctx.lib.tc_orient_by(ctx.handle, n, m, _ptr(edges) if m else None, _ptr(keys), _ptr(offsets),
                                        _ptr(cols), _ptr(deg), _ptr(dhat), _ptr(ws), ws.numel(), _stream(dev)))
     return Graph(n, m, offsets, cols[:m], deg[:n], dhat[:n])
+
+
+def orient_host(edges_host: torch.Tensor, n: int, ctx: Context | None = None,
+                edges_dev: torch.Tensor | None = None) -> tuple[Graph, torch.Tensor]:
+    """tc_orient_host: edges int32[m, 2] in page-locked host memory -> (oriented CSR, the device copy).
+
+    The copy goes up in chunks on the context's copy stream while the degree pass
+    counts the chunks already there.  edges_dev (int32[m, 2] on the device) is
+    reused when given, else allocated."""
+    ctx = ctx or default_context()
+    dev = ctx.device
+    if edges_host.device.type != "cpu" or edges_host.dtype != torch.int32 or edges_host.dim() != 2 \
+            or edges_host.shape[1] != 2 or not edges_host.is_contiguous():
+        raise ValueError("edges_host must be a contiguous int32 [m, 2] tensor in host memory")
+    m = int(edges_host.shape[0])
+    if edges_dev is None:
+        edges_dev = torch.empty((max(m, 1), 2), dtype=torch.int32, device=dev)
+    elif edges_dev.device != dev or edges_dev.dtype != torch.int32 or edges_dev.numel() < 2 * m \
+            or not edges_dev.is_contiguous():
+        raise ValueError("edges_dev must be a contiguous int32 tensor of at least [m, 2] on the context's device")
+    offsets = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    cols = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+    deg = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    dhat = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    ws = ctx.workspace(TC_OP_ORIENT, n, m)
+    ctx.check(ctx.lib.tc_orient_host(ctx.handle, n, m, edges_host.data_ptr() if m else None,
+                                     _ptr(edges_dev) if m else None, _ptr(offsets), _ptr(cols), _ptr(deg),
+                                     _ptr(dhat), _ptr(ws), ws.numel(), _stream(dev)))
+    return Graph(n, m, offsets, cols[:m], deg[:n], dhat[:n]), edges_dev[:m]
 
 
 def count(g: Graph, ctx: Context | None = None, out: torch.Tensor | None = None) -> int:

@@ -325,6 +325,31 @@ tc_status tc_orient_by(tc_ctx* ctx, int32_t n, int64_t m, const int32_t* edges, 
   return finish(ctx, s, tc::launch_orient(ctx, n, m, edges, offsets, cols, deg, dhat, w, s, keys_dev));
 }
 
+tc_status tc_orient_host(tc_ctx* ctx, int32_t n, int64_t m, const int32_t* edges_host, int32_t* edges_dev,
+                         int64_t* offsets, int32_t* cols, int32_t* deg, int32_t* dhat, void* ws, size_t ws_bytes,
+                         tc_stream stream) {
+  if (!ctx) return TC_ERR_INVALID_ARG;
+  if (n < 0 || m < 0) return fail(ctx, TC_ERR_INVALID_ARG, "negative n or m");
+  if (!offsets || (n > 0 && (!deg || !dhat)) || (m > 0 && (!edges_host || !edges_dev || !cols)))
+    return fail(ctx, TC_ERR_INVALID_ARG, "NULL buffer");
+  if (m > 0 && !aligned(edges_dev, 8)) return fail(ctx, TC_ERR_INVALID_ARG, "edges_dev not 8-byte aligned");
+  if (!aligned(offsets, 8)) return fail(ctx, TC_ERR_INVALID_ARG, "offsets not 8-byte aligned");
+  if (m > 0) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, edges_host) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+      cudaGetLastError();
+      return fail(ctx, TC_ERR_INVALID_ARG, "edges_host is not page-locked host memory");
+    }
+  }
+  tc_status st = check_ws(ctx, TC_OP_ORIENT, n, m, ws, ws_bytes);
+  if (st != TC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = begin(ctx, s)) != TC_OK) return st;
+  Carver c(ws);
+  tc::OrientWs w = tc::carve_orient(c, n, m);
+  return finish(ctx, s, tc::launch_orient(ctx, n, m, edges_dev, offsets, cols, deg, dhat, w, s, nullptr, edges_host));
+}
+
 static tc_status count_impl(tc_ctx* ctx, const tc_graph* g, uint64_t* total_dev, int64_t* tv_dev, double* cc_dev,
                             void* ws, size_t ws_bytes, cudaStream_t s) {
   tc_status st = check_graph(ctx, g);

@@ -207,9 +207,13 @@ cudaError_t exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, ScanW
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, ScanWs ws, cudaStream_t s);
 
 // keys: NULL for the degree order of Eq. (1), else v precedes u iff (keys[v], v) < (keys[u], u).
+// edges_host: when set, `edges` is filled from this page-locked copy in chunks on the
+// context's copy stream, each chunk counted by the degree pass as soon as it lands.
 cudaError_t launch_orient(Ctx* ctx, int32_t n, int64_t m, const int32_t* edges, int64_t* offsets,
                           int32_t* cols, int32_t* deg, int32_t* dhat, OrientWs ws, cudaStream_t s,
-                          const int64_t* keys = nullptr);
+                          const int64_t* keys = nullptr, const int32_t* edges_host = nullptr);
+// The context's copy stream and its five events (created on first use).
+cudaError_t ensure_copy_stream(Ctx* ctx);
 
 enum CountMode { MODE_COUNT = 0, MODE_LOCAL = 1, MODE_LIST_COUNT = 2, MODE_LIST_WRITE = 3 };
 

@@ -59,14 +59,14 @@ bool cut_ranges(int32_t n, const int64_t* off, int64_t cap, std::vector<std::pai
   return true;
 }
 
+}  // namespace
+
 cudaError_t ensure_copy_stream(Ctx* ctx) {
   if (ctx->copy_stream) return cudaSuccess;
   cudaError_t e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
   for (int i = 0; e == cudaSuccess && i < 5; ++i) e = cudaEventCreateWithFlags(&ctx->copy_ev[i], cudaEventDisableTiming);
   return e;
 }
-
-}  // namespace
 
 cudaError_t launch_count_streamed(Ctx* ctx, int32_t n, int64_t m, const int64_t* off_h, const int32_t* cols_h,
                                   uint64_t* total, int64_t* tv, StreamWs w, cudaStream_t s, const char** why) {

@@ -155,6 +155,42 @@ def test_orientation_over_large_id_ranges(tc, make):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("make", [
+    lambda: (1 << 21, synth.er(1 << 21, 20_000_000, 72)),                 # two copy chunks, the second ragged
+    lambda: (1 << 14, synth.shuffle_edges(synth.rmat(14, 16, 73), 74)),   # one chunk
+    lambda: (300, synth.complete(300)),
+    lambda: (9, np.zeros((0, 2), np.int32)),
+])
+def test_orientation_from_host_memory(tc, make):
+    # tc_orient_host gives the same CSR, d_v and dhat_v as tc_orient, and leaves the edges on the device
+    n, e = make()
+    host = torch.from_numpy(np.ascontiguousarray(e, dtype=np.int32)).pin_memory()
+    g, ed = tc.orient_host(host, n)
+    ref = tc.orient(to_dev(e), n)
+    for a, b in ((g.offsets, ref.offsets), (g.cols, ref.cols), (g.deg, ref.deg), (g.dhat, ref.dhat)):
+        assert torch.equal(a, b)
+    assert torch.equal(ed.cpu(), host)
+    if len(e) < 10 ** 6:
+        check_orient(tc, n, e, g)
+    # a second call reuses the device buffer
+    g2, ed2 = tc.orient_host(host, n, edges_dev=ed)
+    assert ed2.data_ptr() == ed.data_ptr() and torch.equal(g2.cols, ref.cols)
+
+
+def test_orientation_from_host_memory_reports_errors(tc):
+    e = synth.er(1 << 21, 20_000_000, 75)
+    bad = e.copy()
+    bad[-5] = (7, 1 << 21)  # an id outside [0, n) in the second chunk
+    with pytest.raises(tc.TcError) as ex:
+        tc.orient_host(torch.from_numpy(bad).pin_memory(), 1 << 21)
+    assert ex.value.status == 2
+    with pytest.raises(tc.TcError) as ex:  # pageable host memory is refused before anything is queued
+        tc.orient_host(torch.from_numpy(e[:1000].copy()), 1 << 21)
+    assert ex.value.status == 1
+    g, _ = tc.orient_host(torch.from_numpy(e).pin_memory(), 1 << 21)  # the context is still usable
+    assert int(g.dhat.sum()) == len(e)
+
+
 def test_single_triangle_with_isolated_vertices(tc):
     check_all(tc, 10, np.array([[5, 2], [2, 9], [9, 5]], np.int32))
 
