@@ -167,6 +167,22 @@ def cpu_oracle_pipeline(n, e, q, seed):
     return time.perf_counter() - t0, len(e), r["T"]
 
 
+def cpu_parallel_pipeline(n, e, q, seed):
+    """The same step on all host cores: the parallel oracle's adjacency, orientation,
+    NodeIteratorN (Figure 2) with T_v, the listing, clustering and the sparsified
+    count.  Returns (seconds, m, T, threads)."""
+    import oracle
+    from oracle import par
+    t0 = time.perf_counter()
+    adj = par.adjacency(n, e)
+    off, cols, _ = par.orient(adj)
+    r = par.count(n, off, cols, local=True)
+    par.listing(n, off, cols, r["apex"])
+    oracle.clustering(adj.deg, r["tv"])
+    par.sparsify_count(n, e, adj.deg, seed, q)
+    return time.perf_counter() - t0, len(e), r["T"], par.num_threads()
+
+
 def run_reference(args, rank):
     if rank != 0:
         return 0
@@ -795,6 +811,8 @@ def main():
     ap.add_argument("--also-e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-log-n", type=int, default=20, help="log2 n of the CPU-baseline sample")
+    ap.add_argument("--cpu-par-log-n", type=int, default=22,
+                    help="log2 n of the all-cores CPU-baseline sample (0: skip)")
     ap.add_argument("--ref-log-n", type=int, default=18, help="log2 n of each reference-arm step")
     ap.add_argument("--batch-graphs", type=int, default=4096,
                     help="graphs of the batched Chung-Lu workload (0 skips the batched measurement)")
@@ -876,6 +894,15 @@ def main():
             cpu = {"value": sm / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"CPU oracle (NodeIterator++, 1 thread) full step on PA(n=2^{args.cpu_log_n}, "
                              f"k=16), m={sm}: adjacency, T, T_v, listing, C_v, sparsified count; {dt:.1f} s"}
+            if args.cpu_par_log_n > 0:
+                pn = 1 << args.cpu_par_log_n
+                pe = synth.ba(pn, 16, args.seed)
+                pdt, pm, _, threads = cpu_parallel_pipeline(pn, pe, args.q, args.seed)
+                cpu["all_cores"] = {
+                    "value": pm / pdt, "unit": UNIT, "cores": threads, "kind": "oracle (OpenMP NodeIteratorN)",
+                    "sample": f"parallel CPU oracle (NodeIteratorN, {threads} threads) full step on "
+                              f"PA(n=2^{args.cpu_par_log_n}, k=16), m={pm}: adjacency, orientation, T, T_v, "
+                              f"listing, C_v, sparsified count; {pdt:.1f} s"}
         out = {
             "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
