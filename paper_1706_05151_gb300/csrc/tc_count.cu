@@ -361,8 +361,10 @@ __device__ __forceinline__ uint32_t tile_batch(TileSmem<MODE, SH>& sm, int top, 
   int tot;
   bool is_short;
   int32_t len;
-  batch_setup(bs, a, ws, u, act, eg, vl, lo, vlen, tot, is_short, len, err, MODE == MODE_LIST_WRITE, 0u,
-              vbase + vl, vlen, a.hub_min > 0 ? (a.reuse_hub ? 1 : 2) : 0);
+  // an apex with one out-neighbour closes no triangle (N_v and N_u meet at most in u, and
+  // u is not in N_u): its edge reads no list, and the hub side never sees it either
+  batch_setup(bs, a, ws, u, act && vlen >= 2, eg, vl, lo, vlen, tot, is_short, len, err, MODE == MODE_LIST_WRITE,
+              0u, vbase + vl, vlen, a.hub_min > 0 ? (a.reuse_hub ? 1 : 2) : 0);
   int qn = 0;
   // candidate lists are read evict-first: a list is read again only after many others,
   // and the lines it would keep are better spent on the list bounds (read evict-last)
