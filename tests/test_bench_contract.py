@@ -84,3 +84,15 @@ def test_serving_size_classes_and_request_weights():
     assert abs(p.sum() - 1.0) < 1e-12 and all(a > b for a, b in zip(p, p[1:]))
     # proportional to m^(-1/2): the ratio of two graphs' shares is the root of their sizes' ratio
     assert abs(p[0] / p[3] - (ms[3] / ms[0]) ** 0.5) < 1e-9
+
+
+def test_cpu_baselines_agree_on_the_sample_they_time():
+    # the single-core and all-cores CPU baselines run the same step: the same T on the same graph
+    import bench
+    import synth
+    n = 1 << 12
+    e = synth.ba(n, 8, 3)
+    dt, m, T = bench.cpu_oracle_pipeline(n, e, 0.1, 3)
+    pdt, pm, pT, threads = bench.cpu_parallel_pipeline(n, e, 0.1, 3)
+    assert (m, T) == (pm, pT) and T > 0
+    assert threads >= 1 and dt > 0 and pdt > 0
