@@ -667,7 +667,10 @@ tc_status tc_capture_begin(tc_ctx* ctx, tc_stream stream) {
   if (!stream) return fail(ctx, TC_ERR_INVALID_ARG, "the legacy default stream cannot be captured");
   if (ctx->capturing) return fail(ctx, TC_ERR_INVALID_ARG, "capture already in progress");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, TC_ERR_CUDA, "cudaSetDevice failed");
-  cudaError_t e = cudaStreamBeginCapture(static_cast<cudaStream_t>(stream), cudaStreamCaptureModeThreadLocal);
+  // tc_orient_host forks its copies onto the context's copy stream: create it outside the capture
+  cudaError_t e = tc::ensure_copy_stream(ctx);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream");
+  e = cudaStreamBeginCapture(static_cast<cudaStream_t>(stream), cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "begin capture");
   ctx->capturing = 1;
   ctx->capture_status = TC_OK;

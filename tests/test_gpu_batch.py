@@ -144,3 +144,43 @@ def test_capture_refuses_synchronizing_calls(tc):
     # the context works normally afterwards
     assert tc.count(g, ctx) == 120
     ctx.close()
+
+
+def test_host_memory_orientation_can_be_captured(tc):
+    """tc_orient_host inside tc_capture_begin/end on a fresh context: the chunked copies
+    (two chunks here) join the recorded sequence, and each replay reads the page-locked
+    buffer as it is then -- refilled between replays with a relabelled graph of the same size."""
+    ctx = tc.Context(0)
+    n = 1 << 21
+    e1 = synth.er(n, 20_000_000, 83)
+    m = len(e1)
+    perm = np.random.default_rng(84).permutation(n).astype(np.int32)
+    e2 = np.ascontiguousarray(perm[e1])
+    host = torch.from_numpy(e1.copy()).pin_memory()
+    dev = torch.device("cuda")
+    ed = torch.empty((m, 2), dtype=torch.int32, device=dev)
+    offsets = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    cols = torch.empty(m, dtype=torch.int32, device=dev)
+    deg = torch.empty(n, dtype=torch.int32, device=dev)
+    dhat = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = ctx.workspace(tc.TC_OP_ORIENT, n, m)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    lib, P = ctx.lib, tc._ptr
+    sp = tc.ctypes.c_void_p(s.cuda_stream)
+    assert lib.tc_capture_begin(ctx.handle, sp) == 0
+    st = lib.tc_orient_host(ctx.handle, n, m, host.data_ptr(), P(ed), P(offsets), P(cols), P(deg), P(dhat),
+                            P(ws), ws.numel(), sp)
+    x = tc.ctypes.c_void_p()
+    assert lib.tc_capture_end(ctx.handle, sp, tc.ctypes.byref(x)) == 0 and st == 0
+    try:
+        for e in (e1, e2):
+            host.copy_(torch.from_numpy(e))
+            assert lib.tc_exec_launch(x, sp) == 0
+            s.synchronize()
+            ref = tc.orient(torch.from_numpy(e).cuda(), n, ctx)
+            assert torch.equal(offsets, ref.offsets) and torch.equal(cols, ref.cols)
+            assert torch.equal(deg, ref.deg) and torch.equal(dhat, ref.dhat)
+    finally:
+        lib.tc_exec_destroy(x)
+        ctx.close()
