@@ -442,10 +442,20 @@ __global__ void __launch_bounds__(kTileWarps * 32, 8) k_count_tile(CountArgs a, 
   TileSmem<MODE, SH>& sm = s_t[wid];
   unsigned long long acc = 0;
   const uint64_t stream = l2_policy_evict_first();
+  uint32_t claim_next = 0;
+  int claim_left = 0;
   for (int32_t chunk = 0; a.tile_quota <= 0 || chunk < a.tile_quota; ++chunk) {
-    uint32_t off = 0;
-    if (lane == 0) off = atomicAdd(&ws.counters[kCtrCursor], 32u);
-    off = __shfl_sync(FULL, off, 0);
+    if (claim_left == 0) {
+      // every warp claims its chunks from one counter, and additions to one address
+      // serialize in L2: a pass over many vertices claims tile_claim chunks at a time
+      uint32_t c0 = 0;
+      if (lane == 0) c0 = atomicAdd(&ws.counters[kCtrCursor], 32u * static_cast<uint32_t>(a.tile_claim));
+      claim_next = __shfl_sync(FULL, c0, 0);
+      claim_left = a.tile_claim;
+    }
+    const uint32_t off = claim_next;
+    claim_next += 32u;
+    --claim_left;
     if (off >= static_cast<uint32_t>(a.v_hi - a.v_lo)) break;
     const uint32_t base = static_cast<uint32_t>(a.v_lo) + off;  // apex vertices [v_lo, v_hi) only
     const int32_t v = static_cast<int32_t>(base) + lane;
@@ -1093,8 +1103,17 @@ cudaError_t launch_tile(Ctx* ctx, const CountArgs& a, CountWs ws, cudaStream_t s
       : static_cast<int>(min64(
             persistent_blocks(ctx, reinterpret_cast<const void*>(&k_count_tile<MODE, SH>), kTileWarps * 32, 0),
             max64(1, (chunks + kTileWarps - 1) / kTileWarps)));
+  // chunks per claim, at most 8: the counting passes keep at least 64 claims per warp (their
+  // chunks are heavy, and coarser claims leave the last warps with more work: PA 2^24 per-vertex
+  // pass 10.79 -> 10.98 ms with 6 chunks per claim); the listing write pass, which skips almost
+  // every apex of a sparse listing, at least 16 (PA 2^27: 8.56 -> 2.64 ms with 8)
+  const int64_t min_claims = MODE == MODE_LIST_WRITE ? 16 : 64;
+  CountArgs b = a;
+  b.tile_claim = a.tile_quota > 0
+      ? 1
+      : static_cast<int32_t>(min64(8, max64(1, chunks / (static_cast<int64_t>(tgrid) * kTileWarps * min_claims))));
   Stage st(ctx, s, name);
-  k_count_tile<MODE, SH><<<tgrid, kTileWarps * 32, 0, s>>>(a, ws, ctx->d_err);
+  k_count_tile<MODE, SH><<<tgrid, kTileWarps * 32, 0, s>>>(b, ws, ctx->d_err);
   counted(ctx);
   return cudaSuccess;
 }

@@ -231,6 +231,7 @@ struct CountArgs {
   int32_t tile_max = 0;                       // lists longer than this go to the block kernel (set by launch_count)
   int32_t hub_min = 0;                        // hub side for lists of at least this length (0: off; set by launch_count)
   int32_t tile_quota = 0;                     // chunks per warp before its block retires (0: until the work ends)
+  int32_t tile_claim = 1;                     // 32-vertex chunks a warp of the tile kernel claims at once (set by launch_count)
   const int32_t* off32 = nullptr;             // int32 copy of offsets (set by launch_count when m < 2^31)
   int32_t v_lo = 0, v_hi = -1;                // apex vertices counted: [v_lo, v_hi) (-1: n)
   bool off32_ready = false;                   // off32 already holds these offsets (a sequence of calls on one graph)
